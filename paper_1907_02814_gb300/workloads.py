@@ -1,0 +1,273 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws random particle populations (energies, directions,
+weights, occupancies, identifiers) and plasma parameters.  It contains none
+of the collision method's arithmetic, so both the CUDA path and the CPU
+oracle consume its output.
+
+Momenta are proper velocities u = p/(m c) (photons: k times the direction,
+k in m_e c^2); weights are densities in m^-3 so that n = sum of weights in a
+cell; identifiers are unique per species and below 2^63.
+
+Shapes follow the paper's validation beam (Sec. III.A, Fig. valid_brem_tf)
+and its copper-foil runs (Sec. IV): a 1 MeV exponential electron source on
+solid Cu, a power-law source on Au of varying ionization, and a
+log-normal-occupancy batch of about 2e8 electrons over 2^20 cells.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MEC2_MEV = 0.51099895000          # electron rest energy, MeV
+AMU_ME = 1822.888486209           # atomic mass unit in electron masses
+MASS_CU = 63.546 * AMU_ME
+MASS_AU = 196.966570 * AMU_ME
+MASS_TA = 180.94788 * AMU_ME
+MASS_AL = 26.9815385 * AMU_ME
+
+
+@dataclass
+class Material:
+    Z: int
+    Zstar: float
+    n_i: float          # m^-3
+    T_e: float          # eV
+    s_TF: float = 1.0
+    s_D: float = 1.0
+
+
+@dataclass
+class Workload:
+    name: str
+    n_cells: int
+    materials: list
+    material_of_cell: np.ndarray          # int32 [n_cells]
+    ion_mass: float                       # in m_e
+    dt: float                             # s
+    seed: int
+    steps: int
+    species: dict = field(default_factory=dict)   # name -> dict of arrays
+    dx: float = 0.0
+    table: dict = field(default_factory=dict)
+
+    def counts(self, name):
+        return np.bincount(self.species[name]["cell"], minlength=self.n_cells)
+
+
+def _isotropic(rng, n):
+    mu = rng.uniform(-1.0, 1.0, n)
+    phi = rng.uniform(0.0, 2.0 * np.pi, n)
+    s = np.sqrt(1.0 - mu * mu)
+    return s * np.cos(phi), s * np.sin(phi), mu
+
+
+def _lepton_from_T(rng, T):
+    """Isotropic momenta for kinetic energies T (units of m_e c^2)."""
+    p = np.sqrt(T * (T + 2.0))
+    nx, ny, nz = _isotropic(rng, len(T))
+    return p * nx, p * ny, p * nz
+
+
+def _species(ux, uy, uz, w, cell, pid0=0, x=None):
+    n = len(w)
+    return {
+        "ux": np.asarray(ux, np.float32), "uy": np.asarray(uy, np.float32),
+        "uz": np.asarray(uz, np.float32), "w": np.asarray(w, np.float32),
+        "pid": np.arange(pid0, pid0 + n, dtype=np.uint64),
+        "cell": np.asarray(cell, np.int32),
+        "x": None if x is None else np.asarray(x, np.float32),
+    }
+
+
+def empty_species(with_x=False):
+    z = np.zeros(0, np.float32)
+    return {"ux": z, "uy": z, "uz": z, "w": z, "pid": np.zeros(0, np.uint64),
+            "cell": np.zeros(0, np.int32), "x": z.copy() if with_x else None}
+
+
+def _maxwellian_ions(rng, n, T_eV, mass_me):
+    sig = np.sqrt(T_eV / (mass_me * MEC2_MEV * 1e6))
+    return rng.normal(0.0, sig, n), rng.normal(0.0, sig, n), rng.normal(0.0, sig, n)
+
+
+def _shuffle_species(rng, d):
+    """Present particles in random storage order (binning must sort them)."""
+    perm = rng.permutation(len(d["w"]))
+    return {k: (v[perm] if v is not None else None) for k, v in d.items()}
+
+
+def solid_cu(n_cells=64, e_per_cell=64, i_per_cell=64, seed=1, dt=0.1e-15, T_mev=1.0,
+             Zstar=5.0, n_i=8.5e28, T_e=100.0, photons_per_cell=0, beam_gamma=None,
+             shuffle=True):
+    """0D solid-density Cu cells with an exponential (or mono-energetic) electron
+    source, Maxwellian ions at T_i = T_e and uniform weights W = n_i / N_i.
+    ``e_per_cell``/``i_per_cell`` may be ints or per-cell arrays."""
+    rng = np.random.default_rng(seed)
+    ne = np.broadcast_to(np.asarray(e_per_cell), (n_cells,)).astype(np.int64)
+    ni = np.broadcast_to(np.asarray(i_per_cell), (n_cells,)).astype(np.int64)
+    cell_e = np.repeat(np.arange(n_cells), ne)
+    cell_i = np.repeat(np.arange(n_cells), ni)
+    if beam_gamma is None:
+        T = rng.exponential(T_mev / MEC2_MEV, len(cell_e))
+    else:
+        T = np.full(len(cell_e), beam_gamma - 1.0)
+    ux, uy, uz = _lepton_from_T(rng, T)
+    if beam_gamma is not None:
+        ux, uy, uz = np.sqrt(T * (T + 2.0)), np.zeros_like(T), np.zeros_like(T)
+    w_i_cell = n_i / np.maximum(ni, 1)
+    we = np.full(len(cell_e), n_i / 64.0)
+    em = _species(ux, uy, uz, we, cell_e)
+    iux, iuy, iuz = _maxwellian_ions(rng, len(cell_i), T_e, MASS_CU)
+    ion = _species(iux, iuy, iuz, w_i_cell[cell_i], cell_i)
+    npg = np.broadcast_to(np.asarray(photons_per_cell), (n_cells,)).astype(np.int64)
+    cell_g = np.repeat(np.arange(n_cells), npg)
+    # photon energies k ~ k^-2 on [2, 200] m_e c^2
+    u = rng.uniform(0.0, 1.0, len(cell_g))
+    k = 1.0 / (1.0 / 2.0 - u * (1.0 / 2.0 - 1.0 / 200.0))
+    gx, gy, gz = _isotropic(rng, len(cell_g))
+    ph = _species(k * gx, k * gy, k * gz, np.full(len(cell_g), n_i / 64.0), cell_g)
+    if shuffle:
+        em, ion, ph = _shuffle_species(rng, em), _shuffle_species(rng, ion), _shuffle_species(rng, ph)
+    mat = Material(29, Zstar, n_i, T_e)
+    wl = Workload("solid_cu", n_cells, [mat], np.zeros(n_cells, np.int32), MASS_CU, dt, seed, 1)
+    wl.species = {"em": em, "ep": empty_species(), "ph": ph, "ion": ion}
+    return wl
+
+
+def config_plain_cu(seed=1):
+    """64 cells x 64 electrons (exponential, mean 1 MeV, isotropic) + 64 Cu
+    ions per cell, Z* = 5, n_i = 8.5e28 m^-3, T_e = 100 eV, dt = 0.1 fs."""
+    wl = solid_cu(64, 64, 64, seed=seed, dt=0.1e-15)
+    wl.name = "cu_64cells_64e_64i_plain"
+    return wl
+
+
+def thin_target_beam(ratio, n_cells=16, e_per_cell=64, seed=1, dt=1e-15, gamma=None):
+    """Mono-energetic 40 MeV beam through neutral Cu (Fig. valid_brem_tf):
+    n_e = 1e27 m^-3, n_i = 8e28 m^-3 with W_i / W_e = ``ratio``."""
+    rng = np.random.default_rng(seed)
+    g = 1.0 + 40.0 / MEC2_MEV if gamma is None else gamma
+    n_e, n_i = 1e27, 8e28
+    w_e = n_e / e_per_cell
+    w_i = ratio * w_e
+    i_per_cell = int(round(n_i / w_i))
+    cell_e = np.repeat(np.arange(n_cells), e_per_cell)
+    cell_i = np.repeat(np.arange(n_cells), i_per_cell)
+    p = np.sqrt(g * g - 1.0)
+    em = _species(np.full(len(cell_e), p), np.zeros(len(cell_e)), np.zeros(len(cell_e)),
+                  np.full(len(cell_e), w_e), cell_e)
+    ion = _species(np.zeros(len(cell_i)), np.zeros(len(cell_i)), np.zeros(len(cell_i)),
+                   np.full(len(cell_i), n_i / i_per_cell), cell_i)
+    mat = Material(29, 0.0, n_i, 0.0)
+    wl = Workload(f"thin_target_ratio{ratio}", n_cells, [mat], np.zeros(n_cells, np.int32), MASS_CU, dt,
+                  seed, 1)
+    wl.species = {"em": em, "ep": empty_species(), "ph": empty_species(), "ion": ion}
+    return wl
+
+
+def au_foil(n_cells=16384, mean_e=256, i_per_cell=64, seed=2, dt=1e-15, dx=2.4e-9):
+    """1D Au foil: Poisson(mean_e) electrons per cell, kinetic energy ~ E^-2 on
+    0.1-100 MeV, isotropic, weights log-uniform over three decades with mean
+    density 3e25 m^-3; 64 Au ions per cell, Z* integer uniform on [10, 40]
+    (31 material states), n_i = 5.9e28 m^-3, T_e = 1 keV."""
+    rng = np.random.default_rng(seed)
+    ne = rng.poisson(mean_e, n_cells)
+    cell_e = np.repeat(np.arange(n_cells), ne)
+    n = len(cell_e)
+    a, b = 0.1 / MEC2_MEV, 100.0 / MEC2_MEV
+    u = rng.uniform(0.0, 1.0, n)
+    T = 1.0 / (1.0 / a - u * (1.0 / a - 1.0 / b))
+    ux, uy, uz = _lepton_from_T(rng, T)
+    wmean = 3e25 / mean_e
+    w = wmean / (999.0 / (3.0 * np.log(10.0))) * 10.0 ** (3.0 * rng.uniform(0.0, 1.0, n))
+    x = (cell_e + rng.uniform(0.0, 1.0, n)) * dx
+    em = _species(ux, uy, uz, w, cell_e, x=x)
+    zs = rng.integers(10, 41, n_cells)
+    n_i, T_e = 5.9e28, 1000.0
+    mats = [Material(79, float(z), n_i, T_e) for z in range(10, 41)]
+    cell_i = np.repeat(np.arange(n_cells), i_per_cell)
+    iux, iuy, iuz = _maxwellian_ions(rng, len(cell_i), T_e, MASS_AU)
+    xi = (cell_i + rng.uniform(0.0, 1.0, len(cell_i))) * dx
+    ion = _species(iux, iuy, iuz, np.full(len(cell_i), n_i / i_per_cell), cell_i, x=xi)
+    wl = Workload("au_foil", n_cells, mats, (zs - 10).astype(np.int32), MASS_AU, dt, seed, 100, dx=dx)
+    wl.species = {"em": _shuffle_species(rng, em), "ep": empty_species(True),
+                  "ph": empty_species(True), "ion": _shuffle_species(rng, ion)}
+    return wl
+
+
+def lognormal_counts(rng, n_cells, median=64, sigma=1.5, cap=8192):
+    c = np.rint(rng.lognormal(np.log(median), sigma, n_cells))
+    return np.minimum(c, cap).astype(np.int64)
+
+
+def ion_counts(rng, e_counts, total_ions):
+    """Ions spread in proportion to electrons, at least one per occupied cell."""
+    share = e_counts / max(e_counts.sum(), 1)
+    c = np.floor(share * total_ions).astype(np.int64)
+    c = np.where(e_counts > 0, np.maximum(c, 1), 0)
+    return c
+
+
+def batched_cu(n_cells=1 << 20, seed=3, total_ions=30_000_000, photon_frac=0.25, dt=1e-15,
+               median=64, sigma=1.5, cap=8192):
+    """Uneven batch on solid Cu: log-normal electron occupancy (median 64,
+    sigma 1.5, capped at 8192), ions in proportion (>= 1 per occupied cell),
+    photons 0.25 N_e with k ~ k^-2 on [2, 200] m_e c^2, dt = 1 fs.
+    Returns per-cell counts plus a generator of per-cell particle data, so the
+    largest instance can be drawn on the device in chunks."""
+    rng = np.random.default_rng(seed)
+    ce = lognormal_counts(rng, n_cells, median, sigma, cap)
+    ci = ion_counts(rng, ce, total_ions)
+    cg = rng.binomial(ce, photon_frac)
+    return {"e": ce, "i": ci, "g": cg, "seed": seed, "dt": dt,
+            "material": Material(29, 5.0, 8.5e28, 100.0), "ion_mass": MASS_CU,
+            "w_e": 8.5e28 / 64.0, "n_i": 8.5e28, "T_e": 100.0}
+
+
+def batched_cu_host(counts, cells=None):
+    """Host (numpy) particles for the batched workload, optionally only for a
+    subset of cells; the draw for cell c depends on (seed, c) only."""
+    n_cells = len(counts["e"])
+    cells = np.arange(n_cells) if cells is None else np.asarray(cells)
+    out = {k: [] for k in ("em", "ion", "ph")}
+    for c in cells:
+        rng = np.random.default_rng([counts["seed"], int(c)])
+        ne, ni, ng = int(counts["e"][c]), int(counts["i"][c]), int(counts["g"][c])
+        T = rng.exponential(1.0 / MEC2_MEV, ne)
+        ux, uy, uz = _lepton_from_T(rng, T)
+        out["em"].append((ux, uy, uz, np.full(ne, counts["w_e"]), np.full(ne, c)))
+        iux, iuy, iuz = _maxwellian_ions(rng, ni, counts["T_e"], counts["ion_mass"])
+        out["ion"].append((iux, iuy, iuz, np.full(ni, counts["n_i"] / max(ni, 1)), np.full(ni, c)))
+        u = rng.uniform(0.0, 1.0, ng)
+        k = 1.0 / (1.0 / 2.0 - u * (1.0 / 2.0 - 1.0 / 200.0))
+        gx, gy, gz = _isotropic(rng, ng)
+        out["ph"].append((k * gx, k * gy, k * gz, np.full(ng, counts["w_e"]), np.full(ng, c)))
+    res = {}
+    offs = {"em": np.concatenate([[0], np.cumsum(counts["e"])]),
+            "ion": np.concatenate([[0], np.cumsum(counts["i"])]),
+            "ph": np.concatenate([[0], np.cumsum(counts["g"])])}
+    for k, parts in out.items():
+        cat = [np.concatenate([p[i] for p in parts]) if parts else np.zeros(0) for i in range(5)]
+        pid = np.concatenate([np.arange(offs[k][c], offs[k][c + 1]) for c in cells]).astype(np.uint64) \
+            if len(cells) else np.zeros(0, np.uint64)
+        d = _species(*cat[:4], cat[4])
+        d["pid"] = pid
+        res[k] = d
+    res["ep"] = empty_species()
+    return res
+
+
+def emission_params(n_cells=4096, n_samples=512, seed=5):
+    """Differentiable-operator inputs: per-cell Cu plasma parameters
+    (n_i log-uniform on [1e25, 1e29] m^-3, T_e log-uniform on [10, 1e4] eV,
+    Z* uniform on [1, 28], s_TF = s_D = 1) and electron samples with kinetic
+    energy log-uniform on 0.5-200 MeV and unit weights."""
+    rng = np.random.default_rng(seed)
+    n_i = 10.0 ** rng.uniform(25.0, 29.0, n_cells)
+    T_e = 10.0 ** rng.uniform(1.0, 4.0, n_cells)
+    Zs = rng.uniform(1.0, 28.0, n_cells)
+    T = 10.0 ** rng.uniform(np.log10(0.5), np.log10(200.0), (n_cells, n_samples)) / MEC2_MEV
+    return {"n_i": n_i, "T_e": T_e, "Zstar": Zs, "s_TF": np.ones(n_cells), "s_D": np.ones(n_cells),
+            "gamma": 1.0 + T, "w": np.ones((n_cells, n_samples)), "Z": 29}

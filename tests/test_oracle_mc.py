@@ -1,0 +1,282 @@
+"""Pins of the oracle's tables, pairing and Monte Carlo step (Sec. III.A)
+against quadrature, brute force and the paper's analytic thin-target yield
+(Eq. N_br_theo1/2, Fig. valid_brem_tf)."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+from paper_1907_02814_gb300 import workloads as W
+
+C_LIGHT = 299792458.0
+
+
+def quad(f, a, b, **kw):
+    kw.setdefault("epsabs", 0.0)
+    kw.setdefault("epsrel", 1e-11)
+    kw.setdefault("limit", 400)
+    return integrate.quad(f, a, b, **kw)[0]
+
+
+@pytest.fixture(scope="module")
+def cu_tables(orc):
+    spec = orc.table_spec(n_rows=64, n_cols=64)
+    mats = [orc.material(29, 5, 8.5e28, 100.0), orc.material(79, 30, 5.9e28, 1e3)]
+    return orc.OracleTables(mats, spec)
+
+
+# -------------------------------------------------------------- tables ---
+def test_brems_table_matches_quadrature(orc, cu_tables):
+    """sigma_B(T) = int_{x_min}^1 dsigma/dk T dx and the CDF columns equal
+    adaptive quadrature of the oracle's own dsigma/dk (pins the table
+    quadrature, not the formula)."""
+    T = cu_tables
+    sp = T.spec
+    for m in (0, 1):
+        s = T.screening(m)
+        for r in (0, 17, 40, 63):
+            Tk = T.row_value(r)
+            g = 1.0 + Tk
+            f = lambda lx: orc.dsdk_brems(s, g, math.exp(lx) * Tk) * Tk * math.exp(lx)
+            pts = [math.log(0.5)] + [math.log1p(-10.0 ** -j) for j in range(1, 9)]
+            tot = quad(f, math.log(sp.x_min), 0.0, points=pts)
+            assert T.brems_sigma[m, r] == pytest.approx(tot, rel=1e-8)
+            for c in (10, 32, 60):
+                xc = T.col_value(orc.TB_BREMS, c)
+                part = quad(f, math.log(sp.x_min), math.log(xc))
+                assert T.brems_cdf[m, r, c] == pytest.approx(part / tot, rel=1e-8, abs=1e-12)
+
+
+def test_bh_table_matches_quadrature(orc, cu_tables):
+    T = cu_tables
+    s = T.screening(0)
+    for r in (0, 30, 63):
+        kk = 2.0 + T.row_value(r)
+        pts = [1.0 + (kk - 2.0) * 10.0 ** -j for j in range(1, 9)]
+        pts += [kk - 1.0 - (kk - 2.0) * 10.0 ** -j for j in range(1, 9)]
+        tot = quad(lambda g: orc.dsdg_bh(s, kk, g), 1.0, kk - 1.0, points=sorted(pts))
+        assert T.bh_sigma[0, r] == pytest.approx(tot, rel=1e-8)
+        # symmetric plateau: CDF at y = 1/2 is 1/2
+        F = T.bh_cdf[0, r]
+        assert F[0] == 0.0 and F[-1] == 1.0 and np.all(np.diff(F) >= 0)
+
+
+def test_trident_tables_normalised_and_monotone(cu_tables):
+    """Trident pair-energy and split CDFs: parity unpinned beyond being
+    normalised, monotone and (split) symmetric about gamma_p/2."""
+    T = cu_tables
+    for F in (T.tri_gp_cdf, T.tri_split_cdf):
+        assert np.all(F[:, 0] == 0.0) and np.all(F[:, -1] == 1.0)
+        assert np.all(np.diff(F, axis=1) >= 0)
+    n = T.spec.n_cols
+    mid = T.tri_split_cdf[:, :]
+    assert np.allclose(mid + mid[:, ::-1], 1.0, atol=1e-9)
+
+
+def test_sampler_reproduces_row_cdf(orc, cu_tables):
+    """Inverse-CDF sampling at an exact row reproduces that row's CDF (KS)."""
+    T = cu_tables
+    rng = np.random.default_rng(4)
+    r = 40
+    Tk = T.row_value(r)
+    xs = np.array([T.sample(orc.TB_BREMS, 0, Tk, 0.5, u) for u in rng.uniform(size=4000)])
+    grid = np.array([T.col_value(orc.TB_BREMS, c) for c in range(T.spec.n_cols)])
+    F = T.brems_cdf[0, r]
+    cdf = lambda x: np.interp(np.log(x), np.log(grid), F)
+    assert stats.kstest(xs, cdf).pvalue > 1e-3
+    assert xs.min() >= T.spec.x_min and xs.max() <= 1.0
+
+
+def test_sigma_lookup_interpolation(orc, cu_tables):
+    """Log-log interpolation is exact at rows, zero below the table and
+    flags the range above it."""
+    T = cu_tables
+    for r in (0, 5, 63):
+        v, st = T.sigma_lookup(orc.TB_BREMS, 0, T.row_value(r))
+        assert v == pytest.approx(T.brems_sigma[0, r], rel=1e-12) and st == 0
+    assert T.sigma_lookup(orc.TB_BREMS, 0, T.spec.T_min * 0.99)[0] == 0.0
+    v, st = T.sigma_lookup(orc.TB_BREMS, 0, T.spec.T_max * 1.5)
+    assert st & 1 and v == T.brems_sigma[0, -1]
+
+
+# --------------------------------------------------------- permutation ---
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 31, 32, 33, 64, 100, 1000, 8192])
+def test_permutation_is_bijection(orc, n):
+    rk = orc.philox([0, 5, 9, 1], [1, 2])
+    pos = [orc.perm_pos(s, n, rk) for s in range(n)]
+    assert sorted(pos) == list(range(n))
+    for s in range(0, n, max(1, n // 50)):
+        assert orc.perm_elem(pos[s], n, rk) == s
+
+
+@pytest.mark.parametrize("n", [2, 5, 13, 32, 33, 47, 100])
+def test_permutation_uniform(orc, n):
+    """Over many keys every element is equally likely at every position."""
+    draws = 2000 if n <= 47 else 1000
+    cnt = np.zeros((n, n))
+    for t in range(draws):
+        rk = orc.philox([t, 11, 3, 0], [99, 7])
+        for s in range(n):
+            cnt[s, orc.perm_pos(s, n, rk)] += 1
+    chi2 = ((cnt - draws / n) ** 2 / (draws / n)).sum()
+    dof = (n - 1) * (n - 1)
+    assert stats.chi2.sf(chi2, dof) > 1e-4
+
+
+# ----------------------------------------------------------- MC step -----
+def _run(orc, wl, steps, mask, spec=None, cap_extra=20000):
+    spec = spec or orc.table_spec(n_rows=128, n_cols=128)
+    mats = [orc.material(m.Z, m.Zstar, m.n_i, m.T_e, m.s_TF, m.s_D) for m in wl.materials]
+    T = orc.OracleTables(mats, spec)
+    sp = {k: orc.OracleSpecies(v, cap=len(v["w"]) + cap_extra) for k, v in wl.species.items()}
+    ledger = np.zeros((wl.n_cells, 2))
+    tot = None
+    for s in range(steps):
+        _, st = orc.step(T, wl.n_cells, wl.material_of_cell, sp["em"], sp["ep"], sp["ph"], sp["ion"],
+                         wl.ion_mass, wl.dt, wl.seed, s, mask, ledger)
+        assert st["rc"] == 0
+        tot = st if tot is None else {k: (np.add(tot[k], st[k]) if k != "status" else tot[k] | st[k])
+                                      for k in st}
+    return T, sp, ledger, tot
+
+
+@pytest.mark.slow
+def test_thin_target_yield_independent_of_weight_ratio(orc):
+    """Fig. valid_brem_tf: a 40 MeV beam in neutral Cu (n_e = 1e21 cm^-3,
+    n_i = 8e22 cm^-3) radiates N_gamma = n_e n_i v sigma_B t photons
+    (Eq. N_br_theo1) whatever the weight ratio W_i/W_e in {2, 1, 1/2}, and
+    the spectrum follows dsigma_B/dk (Eq. N_br_theo2)."""
+    g = 1.0 + 40.0 / 0.51099895
+    v = C_LIGHT * math.sqrt(1 - 1 / g ** 2)
+    steps, dt, n_cells = 6, 150e-15, 48
+    yields, spectra = {}, {}
+    for ratio in (2.0, 1.0, 0.5):
+        wl = W.thin_target_beam(ratio, n_cells=n_cells, e_per_cell=64, seed=11, dt=dt)
+        T, sp, ledger, st = _run(orc, wl, steps, orc.PROC_BREMS)
+        ph = sp["ph"].as_dict()
+        yields[ratio] = (ledger[:, 1].sum(), len(ph["w"]))
+        spectra[ratio] = np.sqrt(ph["ux"].astype(float) ** 2 + ph["uy"] ** 2 + ph["uz"] ** 2)
+    s = T.screening(0)
+    Tk = g - 1
+    f = lambda lx: orc.dsdk_brems(s, g, math.exp(lx) * Tk) * Tk * math.exp(lx)
+    sigma = quad(f, math.log(1e-7), 0.0)
+    n_e, n_i = 1e27, 8e28
+    expected = n_e * n_i * v * sigma * steps * dt * n_cells       # sum of photon weights over cells
+    for ratio, (wsum, count) in yields.items():
+        rel_err = 1 / math.sqrt(count)
+        assert abs(wsum / expected - 1) < 4 * rel_err + 0.01, (ratio, wsum / expected, count)
+    # spectrum (all ratios pooled) vs dsigma/dk: chi-square in log-k bins
+    ks = np.concatenate(list(spectra.values()))
+    edges = np.exp(np.linspace(math.log(1e-4 * Tk), math.log(Tk), 9))
+    obs = np.histogram(ks, edges)[0]
+    probs = np.array([quad(f, math.log(a / Tk), math.log(b / Tk)) for a, b in zip(edges[:-1], edges[1:])]) / sigma
+    exp_counts = probs / probs.sum() * obs.sum()
+    chi2 = ((obs - exp_counts) ** 2 / exp_counts).sum()
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 0.01
+
+
+@pytest.mark.slow
+def test_radiative_stopping_power_mc(orc):
+    """The MC energy radiated per electron per unit length equals
+    n_i int k dsigma/dk dk (Sec. III.B), within the MC error."""
+    g = 1.0 + 40.0 / 0.51099895
+    wl = W.thin_target_beam(1.0, n_cells=48, e_per_cell=64, seed=12, dt=150e-15)
+    T, sp, ledger, st = _run(orc, wl, 6, orc.PROC_BREMS)
+    ph = sp["ph"].as_dict()
+    k = np.sqrt(ph["ux"].astype(float) ** 2 + ph["uy"] ** 2 + ph["uz"] ** 2)
+    s = T.screening(0)
+    Tk = g - 1
+    f1 = lambda lx: orc.dsdk_brems(s, g, math.exp(lx) * Tk) * Tk * math.exp(lx)
+    fk = lambda lx: f1(lx) * math.exp(lx) * Tk
+    mean_k = quad(fk, math.log(1e-7), 0.0) / quad(f1, math.log(1e-7), 0.0)
+    assert k.mean() == pytest.approx(mean_k, rel=4 * k.std() / k.mean() / math.sqrt(len(k)))
+    # the ledger records the same radiated energy as the photons carry
+    assert ledger[:, 0].sum() == pytest.approx((k * ph["w"]).sum(), rel=1e-6)
+
+
+@pytest.mark.parametrize("mask,dt,boost", [(7, 50e-15, 8.0), (2, 3e-11, 60.0), (4, 1e-11, 1.0)])
+def test_step_conserves_energy_and_charge(orc, mask, dt, boost):
+    """With ions at rest every process conserves sum W*E (leptons with rest
+    mass, photons k) and sum W*q; float32 storage bounds the drift.  The
+    Trident-only and BH-only cases use long steps so that they fire."""
+    wl = W.solid_cu(n_cells=24, e_per_cell=48, i_per_cell=16, seed=5, dt=dt, photons_per_cell=24)
+    for c in ("ux", "uy", "uz"):
+        wl.species["ion"][c][:] = 0
+        wl.species["em"][c] *= boost
+
+    def totals(sp):
+        E = Q = 0.0
+        for name, q in (("em", -1), ("ep", 1), ("ph", 0)):
+            d = sp[name].as_dict()
+            u2 = d["ux"].astype(float) ** 2 + d["uy"].astype(float) ** 2 + d["uz"].astype(float) ** 2
+            e = np.sqrt(u2) if name == "ph" else np.sqrt(1 + u2)
+            E += (d["w"] * e).sum()
+            Q += q * d["w"].astype(float).sum()
+        return E, Q
+
+    spec = orc.table_spec(n_rows=96, n_cols=96)
+    T = orc.OracleTables([orc.material(29, 5, 8.5e28, 100.0)], spec)
+    sp = {k: orc.OracleSpecies(v, cap=len(v["w"]) + 50000) for k, v in wl.species.items()}
+    E0, Q0 = totals(sp)
+    created = np.zeros(5)
+    for s in range(3):
+        _, st = orc.step(T, wl.n_cells, wl.material_of_cell, sp["em"], sp["ep"], sp["ph"], sp["ion"],
+                         wl.ion_mass, wl.dt, wl.seed, s, mask)
+        created += st["created"]
+    E1, Q1 = totals(sp)
+    if mask == 7:
+        assert created[0] > 20
+    if mask == 4:
+        assert created[4] > 20 and sp["ep"].n > 20
+    if mask == 2:
+        assert created[2] > 20 and sp["ep"].n > 20
+    assert E1 == pytest.approx(E0, rel=1e-6)
+    assert Q1 == pytest.approx(Q0, rel=1e-12)
+
+
+def test_step_deterministic_and_cell_sharded(orc):
+    """Random numbers are keyed by (seed, step, cell, slot), so the result does
+    not depend on storage order or on which cells a call covers: running the
+    two halves of the cells separately gives bit-identical particles."""
+    wl = W.solid_cu(n_cells=16, e_per_cell=40, i_per_cell=24, seed=7, dt=400e-15, photons_per_cell=20)
+    spec = orc.table_spec(n_rows=64, n_cols=64)
+    T = orc.OracleTables([orc.material(29, 5, 8.5e28, 100.0)], spec)
+
+    def run(species, cells):
+        sub = {}
+        for k, d in species.items():
+            keep = np.isin(d["cell"], cells)
+            sub[k] = {f: (v[keep] if v is not None else None) for f, v in d.items()}
+        sp = {k: orc.OracleSpecies(v, cap=len(v["w"]) + 5000) for k, v in sub.items()}
+        orc.step(T, wl.n_cells, wl.material_of_cell, sp["em"], sp["ep"], sp["ph"], sp["ion"],
+                 wl.ion_mass, wl.dt, wl.seed, 3)
+        return {k: sp[k].canonical() for k in ("em", "ep", "ph")}
+
+    full = run(wl.species, np.arange(16))
+    a = run(wl.species, np.arange(8))
+    b = run(wl.species, np.arange(8, 16))
+    # shuffled storage order
+    rng = np.random.default_rng(1)
+    shuffled = {}
+    for k, d in wl.species.items():
+        p = rng.permutation(len(d["w"]))
+        shuffled[k] = {f: (v[p] if v is not None else None) for f, v in d.items()}
+    sh = run(shuffled, np.arange(16))
+    for k in ("em", "ep", "ph"):
+        for f in ("ux", "uy", "uz", "w", "pid", "cell"):
+            joined = np.concatenate([a[k][f], b[k][f]])
+            assert np.array_equal(full[k][f], joined)
+            assert np.array_equal(full[k][f], sh[k][f])
+    assert len(full["ph"]["w"]) > 16 * 20      # Brems photons were created
+
+
+def test_case_b_pairs_each_target_once(orc):
+    """N_t > N_p: every ion takes part in exactly one macro-collision and each
+    electron in ceil/floor(N_t/N_p) of them (Sec. III.A, N_ei = max)."""
+    rk = orc.philox([0, 3, 1, 2], [5, 6])
+    Np, Nt = 7, 45
+    targets = [orc.perm_elem(j, Nt, rk) for j in range(Nt)]
+    assert sorted(targets) == list(range(Nt))
+    per_e = np.bincount([j % Np for j in range(Nt)], minlength=Np)
+    assert per_e.max() - per_e.min() <= 1

@@ -1,0 +1,374 @@
+"""Pins of the oracle's cross sections (Sec. II) against what the paper and
+mathematics fix: integral definitions by independent quadrature, textbook
+limits, invariants and the values the paper prints."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+ALPHA = 7.2973525693e-3
+R_E = 2.8179403262e-15
+PI = math.pi
+
+
+def quad(f, a, b, **kw):
+    kw.setdefault("epsabs", 0.0)
+    kw.setdefault("epsrel", 1e-13)
+    kw.setdefault("limit", 400)
+    return integrate.quad(f, a, b, **kw)[0]
+
+
+def yukawa_ff(L):
+    """1 - F_e(u) for a single Yukawa potential, from Eq. (app_FT_FF_V) and
+    Eq. (app_FT_V): (2 pi^2/Z) u^2 Vtilde(u) with Vtilde = Z/(2 pi^2) L^2/(1+L^2 u^2)."""
+    return lambda u: u * u * L * L / (1.0 + L * L * u * u)
+
+
+def tfd_ff(etaTF, LTF, etaD, LD):
+    """1 - F_e(u) for the two-Yukawa TFD potential, Eq. (app_FT_V_TFD)."""
+    return lambda u: u * u * (etaTF * LTF ** 2 / (1 + LTF ** 2 * u * u) + etaD * LD ** 2 / (1 + LD ** 2 * u * u))
+
+
+def I1_def(delta, ff):
+    """Eq. (defphi1) by quadrature."""
+    f = lambda u: (u - delta) ** 2 / u ** 3 * ff(u) ** 2
+    return quad(f, delta, 1.0, points=[min(1.0, 10 * delta)])
+
+
+def I2_def(delta, ff):
+    """Eq. (defphi2) by quadrature."""
+    d = delta
+    f = lambda u: (u ** 3 - 6 * d * d * u * math.log(u / d) + 3 * d * d * u - 4 * d ** 3) / u ** 4 * ff(u) ** 2
+    return quad(f, d, 1.0, points=[min(1.0, 10 * d)])
+
+
+# --------------------------------------------------------------- Philox --
+def test_philox_known_answers(orc):
+    """Philox4x32-10 known-answer vectors (Salmon et al., SC'11; Random123)."""
+    assert orc.philox([0, 0, 0, 0], [0, 0]) == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+    assert orc.philox([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2) == [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]
+    assert orc.philox([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0]) == \
+        [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
+
+
+def test_uniforms_exact_in_float32(orc):
+    rng = np.random.default_rng(0)
+    for r in list(rng.integers(0, 2 ** 32, 2000)) + [0, 255, 256, 2 ** 32 - 1]:
+        u = orc.u01(int(r))
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+
+
+def test_philox_statistics(orc):
+    """Mean and Kolmogorov-Smirnov of 40000 draws on one counter stream."""
+    from scipy import stats
+    us = []
+    for i in range(10000):
+        us += [orc.u01(v) for v in orc.philox([i, 7, 3, 1], [12345, 678])]
+    us = np.array(us)
+    assert abs(us.mean() - 0.5) < 5 * (1 / math.sqrt(12 * len(us)))
+    assert stats.kstest(us, "uniform").pvalue > 1e-3
+
+
+# ------------------------------------------------------- screening (A) --
+def test_lambert_w0(orc):
+    for z in [-1 / math.e + 1e-12, -0.3, -0.1, -1e-3, -1e-8, 0.5, 1.0, 10.0]:
+        w = orc.lambert_w0(z)
+        assert abs(w * math.exp(w) - z) <= 1e-14 * max(1.0, abs(z)) + 1e-15
+    assert abs(orc.lambert_w0(math.e) - 1.0) < 1e-15
+    assert abs(orc.lambert_w0(-1 / math.e) + 1.0) < 1e-7
+
+
+def test_thomas_fermi_and_debye_lengths(orc):
+    """Eq. (LTF): L_TF = a0 Z^-1/3 with a0 = r_C/alpha, so Lbar_TF = Z^-1/3/alpha;
+    Eq. (LDH) with the r_i lower bound; the printed solid-Cu interatomic
+    distance r_i = 1.4e-10 m (Sec. II.B)."""
+    s = orc.screening(orc.material(29, 5, 8.5e28, 100.0))
+    assert s.LTF == pytest.approx(29 ** (-1 / 3) / ALPHA, rel=1e-14)
+    assert s.ri == pytest.approx(1.4e-10, rel=0.01)
+    # at 100 eV the Debye length is below r_i, so L_D is clamped
+    assert s.lambdaD < s.ri
+    assert s.LD == pytest.approx(s.ri / 3.8615926796e-13, rel=1e-14)
+    # the paper: L_D exceeds r_i in solid Cu only above 27 keV (fully ionized)
+    hot = orc.screening(orc.material(29, 29, 8.5e28, 30e3))
+    cold = orc.screening(orc.material(29, 29, 8.5e28, 24e3))
+    assert hot.lambdaD > hot.ri and cold.lambdaD < cold.ri
+    assert s.etaTF + s.etaD == pytest.approx(1.0, abs=1e-16)
+
+
+def test_I_tfd_matches_definition(orc):
+    """Eq. (ITFD) equals quadrature of Eq. (inte) with the TFD form factor."""
+    for (eTF, LTF, eD, LD) in [(1, 44.6, 0, 365), (0.8, 44.6, 0.2, 365), (0.5, 10, 0.5, 3), (0.3, 100, 0.7, 100.0001),
+                               (0.6, 50, 0.4, 50)]:
+        ff = tfd_ff(eTF, LTF, eD, LD)
+        ref = quad(lambda u: u ** 3 * (ff(u) / u ** 2) ** 2, 0.0, 1.0)
+        assert orc.I_tfd(eTF, LTF, eD, LD) == pytest.approx(ref, rel=1e-10)
+
+
+def test_reduced_length(orc):
+    """Eq. (reduit)/(lambert-W): residual, and the limits the paper states
+    (reduced = TF for neutral atoms, = Debye when fully ionized)."""
+    for Zs, T in [(0, 1.0), (5, 100.0), (15, 1e3), (29, 1e4), (28.5, 5e4)]:
+        s = orc.screening(orc.material(29, Zs, 8.5e28, T))
+        a, x = s.ITFD, s.LR ** 2
+        assert 2 * a * (x + 1) == pytest.approx((x + 1) * math.log1p(x) - x, rel=1e-13)
+        # I_R(L_R) from Eq. (inte) for the single Yukawa equals I_TFD
+        ff = yukawa_ff(s.LR)
+        assert quad(lambda u: u ** 3 * (ff(u) / u ** 2) ** 2, 0.0, 1.0) == pytest.approx(a, rel=1e-10)
+    s0 = orc.screening(orc.material(29, 0, 8.5e28, 100.0))
+    assert s0.LR == pytest.approx(s0.LTF, rel=1e-12)
+    sZ = orc.screening(orc.material(29, 29, 8.5e28, 1e4))
+    assert sZ.LR == pytest.approx(sZ.LD, rel=1e-12)
+
+
+def test_coulomb_correction(orc):
+    """f_C = a^2 sum_n 1/(n (n^2 + a^2)), a = alpha Z (Davies-Bethe-Maximon);
+    four zeta terms suffice (Sec. II.B.3)."""
+    for Z in (1, 6, 13, 29, 73, 79, 92):
+        a2 = (ALPHA * Z) ** 2
+        n = np.arange(1, 200001, dtype=np.float64)
+        direct = a2 * np.sum(1.0 / (n * (n * n + a2))) + a2 / (2 * 200000.0 ** 2)
+        assert orc.fC(Z) == pytest.approx(direct, rel=1e-5 if Z <= 79 else 1e-4)
+
+
+# ------------------------------------------------------ Brems (B) --------
+@pytest.mark.parametrize("L", [1.0, 10.0, 44.6, 365.0])
+@pytest.mark.parametrize("delta", [1e-6, 1e-3, 0.05, 0.3, 0.5])
+def test_I1_I2_closed_forms_match_definitions(orc, L, delta):
+    """Eq. (deriv_I1)/(deriv_I2) equal quadrature of Eq. (defphi1)/(defphi2)."""
+    ff = yukawa_ff(L)
+    tol = 1e-9 if L * delta < 50 else 1e-7   # closed form I2 cancels at large L delta
+    assert orc.I1(delta, L) == pytest.approx(I1_def(delta, ff), rel=1e-9, abs=1e-12)
+    assert orc.I2(delta, L) == pytest.approx(I2_def(delta, ff), rel=tol, abs=1e-11)
+
+
+def test_I_unscreened_and_complete_screening_limits(orc):
+    """L -> infinity: I1 -> -ln d - 3/2 + 2d - d^2/2 and
+    I2 -> -ln d - 4/3 - 3 d^2 ln d + 4 d^3/3 (Eq. defphi1/2 with F_e = 0);
+    d -> 0: both -> I_R = [ln(1+L^2) - L^2/(1+L^2)]/2 (Eq. IRE, q_R = q)."""
+    for d in (1e-3, 0.01, 0.1, 0.4):
+        L = 500.0 / d      # corrections O(1/(L d)^2); closed-form rounding O((L d)^3 eps)
+        assert orc.I1(d, L) == pytest.approx(-math.log(d) - 1.5 + 2 * d - d * d / 2, rel=1e-4)
+        assert orc.I2(d, L) == pytest.approx(-math.log(d) - 4 / 3 - 3 * d * d * math.log(d) + 4 * d ** 3 / 3,
+                                             rel=1e-4)
+    for L in (5.0, 54.27, 365.0):
+        IR = 0.5 * (math.log1p(L * L) - L * L / (1 + L * L))
+        assert orc.I1(1e-12, L) == pytest.approx(IR, rel=1e-9)
+        assert orc.I2(1e-12, L) == pytest.approx(IR, rel=1e-9)
+
+
+def _screen(orc, LTF=1e7, LD=1e7, etaTF=1.0, etaD=0.0, LR=1e7, Z=29, fC=0.0):
+    s = orc.Screening()
+    s.Z, s.LTF, s.LD, s.etaTF, s.etaD, s.LR, s.fC = Z, LTF, LD, etaTF, etaD, LR, fC
+    return s
+
+
+@pytest.mark.parametrize("Zs", [0.0, 5.0, 20.0, 29.0])
+@pytest.mark.parametrize("qb", [0, 1])
+def test_nr_closed_form_matches_fourier_integral(orc, Zs, qb):
+    """Eq. (cs_br_nr) equals Eq. (csnr) integrated with Vtilde_TFD of
+    Eq. (app_FT_V_TFD), times the Elwert factor, for both bound readings."""
+    s = orc.screening(orc.material(29, Zs, 8.5e28, 3e4 if Zs > 0 else 1.0))
+    Z = 29
+    for g1 in (1.01, 1.2, 1.6, 2.0):
+        T1 = g1 - 1
+        p1 = math.sqrt(T1 * (T1 + 2))
+        for x in (1e-5, 0.1, 0.5, 0.9):
+            k = x * T1
+            T2 = T1 - k
+            p2 = math.sqrt(T2 * (T2 + 2))
+            if qb == 0:
+                dpp, dpm = p1 + p2, p1 - p2
+            else:
+                dpp, dpm = 2 * p1 - k, k
+            V = lambda u: Z / (2 * PI ** 2) * (s.etaTF * s.LTF ** 2 / (1 + s.LTF ** 2 * u * u)
+                                               + s.etaD * s.LD ** 2 / (1 + s.LD ** 2 * u * u))
+            integral = quad(lambda u: V(u) ** 2 * u ** 3, dpm, dpp)
+            b1, b2 = p1 / g1, p2 / (1 + T2)
+            a = 2 * PI * Z * ALPHA
+            fE = (b1 / b2) * (1 - math.exp(-a / b1)) / (1 - math.exp(-a / b2))
+            ref = 64 * PI ** 4 * R_E ** 2 * ALPHA / (3 * k * p1 * p1) * integral * fE
+            assert orc.dsdk_brems_nr(s, g1, k, qb) == pytest.approx(ref, rel=1e-9)
+
+
+def test_nr_unscreened_born_limit(orc):
+    """Exact bounds + no screening + Z = 1 -> Heitler's NR Born formula
+    16 Z^2 r_e^2 alpha/(3 k p1^2) ln((p1+p2)/(p1-p2)), up to the Elwert factor
+    which is within 1 % of one for Z = 1 at these speeds."""
+    s = _screen(orc, Z=1)
+    for g1 in (1.3, 1.6, 2.0):
+        T1 = g1 - 1
+        p1 = math.sqrt(T1 * (T1 + 2))
+        for x in (0.01, 0.3, 0.7):
+            k = x * T1
+            T2 = T1 - k
+            p2 = math.sqrt(T2 * (T2 + 2))
+            born = 16 * R_E ** 2 * ALPHA / (3 * k * p1 * p1) * math.log((p1 + p2) / (p1 - p2))
+            assert orc.dsdk_brems_nr(s, g1, k, 0) == pytest.approx(born, rel=0.01)
+
+
+def test_nr_elwert_finite_at_tip(orc):
+    """With the exact bounds the Elwert-corrected cross section stays finite
+    as the outgoing momentum vanishes."""
+    s = orc.screening(orc.material(29, 5, 8.5e28, 100.0))
+    g1 = 1.5
+    vals = [orc.dsdk_brems_nr(s, g1, (1 - e) * 0.5, 0) for e in (1e-4, 1e-6, 1e-8)]
+    assert all(np.isfinite(vals))
+    assert vals[2] == pytest.approx(vals[1], rel=1e-2)
+
+
+def test_relativistic_unscreened_limit(orc):
+    """No screening, delta -> 0: Eq. (csre) -> the unscreened extreme
+    relativistic Bethe-Heitler Brems spectrum
+    4 Z^2 r_e^2 alpha/k (1 + eps^2 - 2 eps/3)(ln(2 g1 g2/k) - 1/2)."""
+    s = _screen(orc, LR=1e6)
+    Z = 29
+    for g1 in (50.0, 90.0):
+        for k in (0.05, 0.5, 2.0):
+            g2 = g1 - k
+            eps = g2 / g1
+            ref = 4 * Z * Z * R_E ** 2 * ALPHA / k * (1 + eps * eps - 2 * eps / 3) * (math.log(2 * g1 * g2 / k) - 0.5)
+            assert orc.dsdk_brems_rel(s, g1, k, 0.0) == pytest.approx(ref, rel=2e-3)
+
+
+def test_complete_screening_limit(orc):
+    """delta -> 0 with screening: Eq. (csre) -> 4 Z^2 r_e^2 alpha/k
+    {(1+eps^2)(I_R+1) - (2/3) eps (I_R + 5/6)}, I_R from Eq. (IRE); the UR
+    form subtracts f_C in both brackets (Eq. csur)."""
+    s = orc.screening(orc.material(29, 5, 8.5e28, 100.0))
+    L = s.LR
+    IR = 0.5 * (math.log1p(L * L) - L * L / (1 + L * L))
+    Z = 29
+    g1 = 1e5
+    for k in (1e-2, 1.0):
+        eps = (g1 - k) / g1
+        ref = 4 * Z * Z * R_E ** 2 * ALPHA / k * ((1 + eps ** 2) * (IR + 1) - 2 / 3 * eps * (IR + 5 / 6))
+        assert orc.dsdk_brems_rel(s, g1, k, 0.0) == pytest.approx(ref, rel=1e-6)
+        refc = 4 * Z * Z * R_E ** 2 * ALPHA / k * ((1 + eps ** 2) * (IR + 1 - s.fC) - 2 / 3 * eps * (IR + 5 / 6 - s.fC))
+        assert orc.dsdk_brems(s, g1, k) == pytest.approx(refc, rel=1e-6)
+
+
+def test_regime_selection(orc):
+    """NR for gamma <= 2, relativistic up to 100, Coulomb-corrected above."""
+    s = orc.screening(orc.material(29, 5, 8.5e28, 100.0))
+    assert orc.dsdk_brems(s, 2.0, 0.3) == orc.dsdk_brems_nr(s, 2.0, 0.3)
+    assert orc.dsdk_brems(s, 2.0001, 0.3) == orc.dsdk_brems_rel(s, 2.0001, 0.3, 0.0)
+    assert orc.dsdk_brems(s, 100.0, 3.0) == orc.dsdk_brems_rel(s, 100.0, 3.0, 0.0)
+    assert orc.dsdk_brems(s, 100.5, 3.0) == orc.dsdk_brems_rel(s, 100.5, 3.0, s.fC)
+    assert orc.dsdk_brems(s, 10.0, 9.0) == 0.0 and orc.dsdk_brems(s, 10.0, 0.0) == 0.0
+
+
+def test_cutoff_energy_fraction(orc):
+    """Sec. III.A: with x in (1e-7, 1) the energy radiated below the cut-off
+    is a negligible fraction (about 1e-5 or less) of the total."""
+    s = orc.screening(orc.material(29, 5, 8.5e28, 100.0))
+    for T_mev in (0.1, 1.0, 100.0):
+        T = T_mev / 0.51099895
+        g = 1 + T
+        f = lambda lx: orc.dsdk_brems(s, g, math.exp(lx) * T) * (math.exp(lx) * T) ** 2
+        below = quad(f, math.log(1e-14), math.log(1e-7))
+        total = quad(f, math.log(1e-14), 0.0, points=[math.log(0.5), math.log(0.99)])
+        assert below / total <= 1e-5
+
+
+def test_radiative_stopping_rises_with_ionization(orc):
+    """Sec. II.B: the radiative stopping power of solid Cu rises with the
+    temperature, more at higher energy (+7 %, +12 %, +37 % from 0 to 10 keV
+    at 100 keV, 5 MeV, 100 MeV).  Z* = Z stands in for the hot state."""
+    cold = orc.screening(orc.material(29, 0.0, 8.5e28, 1.0))
+    hot = orc.screening(orc.material(29, 29.0, 8.5e28, 1e4))
+    rises = []
+    for T_mev in (0.1, 5.0, 100.0):
+        T = T_mev / 0.51099895
+        g = 1 + T
+        def srad(s):
+            f = lambda lx: orc.dsdk_brems(s, g, math.exp(lx) * T) * (math.exp(lx) * T) ** 2
+            return quad(f, math.log(1e-7), 0.0, points=[math.log(0.5)])
+        rises.append(srad(hot) / srad(cold) - 1)
+    assert 0 < rises[0] < rises[1] < rises[2]
+    for got, paper in zip(rises, (0.07, 0.12, 0.37)):
+        assert paper / 3 < got < 3 * paper
+
+
+# ---------------------------------------------------------- pairs (C, D) --
+def test_bh_symmetry_threshold_and_unscreened_limit(orc):
+    """Eq. (dsdkbh): symmetric under gamma_+ <-> k - gamma_+ (Sec. II.C);
+    zero outside 1 < gamma_+ < k-1; with no screening and delta -> 0 the
+    textbook 4 Z^2 r_e^2 alpha/k^3 (g+^2 + g-^2 + 2/3 g+ g-)(ln(2 g+ g-/k) - 1/2)."""
+    s = orc.screening(orc.material(29, 5, 8.5e28, 100.0))
+    for k in (2.5, 10.0, 200.0):
+        for y in (0.05, 0.3, 0.49):
+            gp = 1 + y * (k - 2)
+            assert orc.dsdg_bh(s, k, gp) == pytest.approx(orc.dsdg_bh(s, k, k - gp), rel=1e-12)
+    assert orc.dsdg_bh(s, 10.0, 1.0) == 0.0 and orc.dsdg_bh(s, 10.0, 9.0) == 0.0
+    u = _screen(orc, LR=1e6)
+    Z = 29
+    for k in (2e4, 1e5):
+        for frac in (0.2, 0.5):
+            gp = frac * k
+            gm = k - gp
+            ref = 4 * Z * Z * R_E ** 2 * ALPHA / k ** 3 * (gp * gp + gm * gm + 2 / 3 * gp * gm) * \
+                (math.log(2 * gp * gm / k) - 0.5)
+            assert orc.dsdg_bh(u, k, gp) == pytest.approx(ref, rel=1e-3)
+
+
+def test_bh_total_vanishes_at_threshold(orc):
+    s = orc.screening(orc.material(29, 5, 8.5e28, 100.0))
+    tot = [quad(lambda g: orc.dsdg_bh(s, k, g), 1.0, k - 1.0, epsrel=1e-10) for k in (2.0001, 2.01, 2.1)]
+    # the gamma_+ range shrinks to zero: sigma_BH ~ (k - 2) near threshold
+    assert tot[0] < tot[1] < tot[2] and tot[0] < 3e-3 * tot[2]
+
+
+def test_trident_total(orc):
+    """Sec. II.D fit: zero below the pair threshold gamma = 3, positive and
+    increasing above (values unpinned beyond the fit itself)."""
+    assert orc.sigma_trident(29, 2.9) == 0.0
+    v = [orc.sigma_trident(29, g) for g in (3.0, 10.0, 100.0, 1000.0)]
+    assert all(a < b for a, b in zip(v, v[1:])) and v[0] > 0
+    assert orc.sigma_trident(58, 10.0) == pytest.approx(4 * orc.sigma_trident(29, 10.0), rel=1e-14)
+
+
+def test_trident_shapes(orc):
+    """Pair-energy spectrum vanishes at threshold and at the kinematic edge;
+    the split shape is symmetric in gamma_+ <-> gamma_p - gamma_+ and not
+    negative (parity unpinned beyond these properties)."""
+    for g1 in (5.0, 50.0, 500.0):
+        assert orc.dsdgp_trident(29, g1, 2.0) == 0.0 and orc.dsdgp_trident(29, g1, g1 - 1.0) == 0.0
+        assert orc.dsdgp_trident(29, g1, 0.5 * (g1 + 1)) > 0
+    for gp in (3.0, 6.0, 60.0):
+        for y in (0.1, 0.3):
+            a = 1 + y * (gp - 2)
+            assert orc.split_shape(gp, a) == pytest.approx(orc.split_shape(gp, gp - a), rel=1e-12)
+            assert orc.split_shape(gp, a) >= 0
+
+
+# --------------------------------------------------------- kinematics ----
+def test_lorentz_transform(orc):
+    """Sec. III.A transform into the ion frame (with the ion velocity as the
+    last factor): invariant mass, gamma' = g_e g_i (1 - beta_e . beta_i), and
+    the inverse transform restores the input."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        ue = rng.normal(0, 3, 3)
+        ui = rng.normal(0, 0.3, 3)
+        ge, gi = math.sqrt(1 + ue @ ue), math.sqrt(1 + ui @ ui)
+        out = orc.boost(ui, np.concatenate([[ge], ue]))
+        assert out[0] ** 2 - out[1:] @ out[1:] == pytest.approx(1.0, rel=1e-10)
+        be, bi = ue / ge, ui / gi
+        assert out[0] == pytest.approx(ge * gi * (1 - be @ bi), rel=1e-12)
+        back = orc.boost(ui, out, inverse=True)
+        assert np.allclose(back, np.concatenate([[ge], ue]), rtol=1e-12, atol=1e-12)
+    # ion at rest: identity
+    v = np.array([2.0, 1.0, -1.0, 1.5])
+    assert np.array_equal(orc.boost(np.zeros(3), v), v)
+
+
+# --------------------------------------------------------- quadrature ----
+def test_gauss_legendre(orc):
+    for n in (1, 2, 8, 16, 64):
+        x, w = orc.gauss_legendre(n)
+        assert w.sum() == pytest.approx(2.0, rel=1e-14)
+        for p in range(0, 2 * n, 3):
+            exact = (1 - (-1) ** (p + 1)) / (p + 1)
+            assert (w * x ** p).sum() == pytest.approx(exact, abs=1e-13)
