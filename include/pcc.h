@@ -1,0 +1,239 @@
+/*
+ * pcc.h -- C ABI of the GB300 (sm_103a) pairwise Coulomb-process collision
+ * library: the per-cell, per-step Monte Carlo Bremsstrahlung, Bethe-Heitler
+ * and Coulomb-Trident step for weighted PIC macro-particles of
+ * B. Martinez et al., arXiv:1907.02814.
+ *
+ * Conventions
+ *   - Momenta are proper velocities u = p/(m c) in float32 (photons store
+ *     k * direction with k in m_e c^2); weights W are densities in m^-3, so
+ *     that the density of a species in a cell is the sum of its weights
+ *     (Sec. III.A); times in seconds; lengths in metres.
+ *   - Every pointer inside a struct or argument marked "device" is CUDA
+ *     device memory owned by the caller; the library never frees it.
+ *   - Every entry point returns a pcc_status code synchronously for argument
+ *     and launch errors.  Conditions found on the device (capacity, table
+ *     range, non-finite values, a wait that gave up) set bits of a sticky
+ *     device status word read by pcc_read_status().
+ *   - Work is enqueued on the given CUDA stream (cudaStream_t passed as
+ *     void*, NULL = default stream); calls are asynchronous unless stated.
+ */
+#ifndef PCC_H
+#define PCC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcc_ctx pcc_ctx;
+
+typedef enum {
+    PCC_OK = 0,
+    PCC_E_INVALID = 1,      /* bad argument (message in pcc_last_error)        */
+    PCC_E_CUDA = 2,         /* a CUDA runtime call failed                       */
+    PCC_E_CAPACITY = 3,     /* a buffer or supported size is too small          */
+    PCC_E_NO_TABLES = 4     /* pcc_collide before pcc_tables_build              */
+} pcc_status;
+
+/* Bits of the device status word (pcc_read_status). */
+#define PCC_ST_TABLE_RANGE 0x1u   /* an energy above the table; the last row was used   */
+#define PCC_ST_PROB_LARGE  0x2u   /* a pair had n sigma v dt > 1 (time step too long)   */
+#define PCC_ST_CAPACITY    0x4u   /* a cell region overflowed; the secondary was dropped */
+#define PCC_ST_NONFINITE   0x8u   /* a non-finite momentum, or a cell or material index
+                                     out of range, was met; that item was skipped       */
+#define PCC_ST_ID_RANGE    0x10u  /* cell >= 2^24, step >= 2^19 or > 65536 pairs per cell:
+                                     secondary identifiers are no longer unique          */
+#define PCC_ST_TIMEOUT     0x20u  /* a bounded wait (bulk copy barrier) gave up          */
+
+typedef enum { PCC_FP64_PLAIN = 0, PCC_FP32_BATCHED = 1 } pcc_precision;
+
+/* Process mask bits for pcc_collide.  The group bits restrict a call to
+ * the electron-ion, positron-ion or photon-ion pairs; when none of them is
+ * set, every group runs. */
+#define PCC_BREMS    0x1u
+#define PCC_TRIDENT  0x2u
+#define PCC_BH       0x4u
+#define PCC_GROUP_EM 0x100u
+#define PCC_GROUP_EP 0x200u
+#define PCC_GROUP_PH 0x400u
+
+/* Plasma state of one material (Sec. II.A): nuclear charge Z, ionization
+ * degree Zstar (an input: the paper's More fit is not given), ion density
+ * n_i [m^-3], temperature T_e [eV], and factors s_TF, s_D multiplying the
+ * Thomas-Fermi (Eq. LTF) and Debye (Eq. LDH, lower bound r_i) lengths
+ * (1 for the paper's model). */
+typedef struct {
+    int Z;
+    double Zstar, n_i, T_e, s_TF, s_D;
+} pcc_material;
+
+/* Table layout (Sec. III.A: tabulated cross sections, inverse CDF).
+ * Rows: the row variable (Brems gamma-1, BH k-2, Trident gamma_1-3,
+ * Trident split gamma_p-2) log-spaced on [gamma_min-1, gamma_max-1].
+ * Columns: Brems x = k/(gamma-1) log-spaced on [10^-cutoff_exp, 1]; BH and
+ * split y linear on [0, 1]; Trident pair energy y = (gamma_p-2)/(gamma_1-3)
+ * log-spaced on [tri_y_min, 1].  quad_nodes Gauss-Legendre points per
+ * column interval.  nr_qbounds 0: momentum-transfer bounds p1 +/- p2;
+ * 1: the printed 2 p1 - k and k (Sec. II.B.1). */
+typedef struct {
+    int n_rows, n_cols, quad_nodes;
+    double gamma_min, gamma_max;
+    int cutoff_exp;
+    double tri_y_min;
+    int nr_qbounds;
+} pcc_table_spec;
+
+/* One species in cell-region layout (all device memory, caller-owned).
+ * Cell c owns slots [cell_start[c], cell_start[c+1]); its live particles
+ * are the first cell_count[c] slots, in ascending pid order.  Secondaries
+ * created during a step are appended after them (cell_added[c]) and become
+ * live at pcc_append_secondaries.  x may be NULL.  capacity = total slots. */
+typedef struct {
+    float *ux, *uy, *uz, *w;
+    float *x;
+    uint64_t *pid;
+    int *cell_start;      /* [n_cells + 1] */
+    int *cell_count;      /* [n_cells]     */
+    int *cell_added;      /* [n_cells]     */
+    int capacity;
+} pcc_species;
+
+/* Unsorted input particles for pcc_bin (device memory, caller-owned). */
+typedef struct {
+    int n;
+    const float *ux, *uy, *uz, *w;
+    const float *x;       /* may be NULL */
+    const uint64_t *pid;  /* unique within the species, < 2^63 */
+    const int *cell;      /* cell index in [0, n_cells) */
+} pcc_particles;
+
+/* Cells: count, material index per cell (device, [n_cells]) and the ion
+ * mass in electron masses. */
+typedef struct {
+    int n_cells;
+    const int *material_of_cell;
+    double ion_mass;
+} pcc_cells;
+
+/* Step counters read back by pcc_read_status (host struct). */
+typedef struct {
+    unsigned long long pairs[3];     /* macro-collisions: e-, e+, photon groups        */
+    unsigned long long accepted[5];  /* U1 < P per channel: Brems e-, Brems e+,
+                                        Trident e-, Trident e+, Bethe-Heitler          */
+    unsigned long long created[5];   /* events kept by the weight correction          */
+    double energy_change;            /* sum over events of W (E_out - E_in), m_e c^2 m^-3 */
+    double charge_change;            /* sum over events of W (q_out - q_in), e m^-3        */
+} pcc_stats;
+
+/* Library version string and the message of the last synchronous error
+ * (thread-local; empty when none). */
+const char *pcc_version(void);
+const char *pcc_last_error(void);
+
+/* Create a context on CUDA device `device`; it owns the tables, the device
+ * status word, step counters and scratch buffers.  Returns PCC_E_CUDA when
+ * the device is unusable.  Destroy with pcc_destroy (NULL is accepted). */
+int  pcc_create(pcc_ctx **out, int device);
+void pcc_destroy(pcc_ctx *ctx);
+
+/* Material preparation and table build, in FP64 on the GPU (Sec. II):
+ * screening lengths (Eq. LTF, LDH with r_i), weights (Eq. V_TFD), I_TFD
+ * (Eq. ITFD), the reduced length (Eq. reduit, lambert-W), f_C (Sec. II.B.3),
+ * then per material the Brems cross section sigma_B and its inverse-CDF
+ * table (Eq. cs_br_nr with the Elwert factor, Eq. csre, Eq. csur with the
+ * reduced I1, I2 of Eq. deriv_I1/I2) and the Bethe-Heitler sigma_BH and
+ * CDF (Eq. dsdkbh); the Trident pair-energy and split CDFs (Sec. II.D) are
+ * shared by all materials.  FP32 copies are made for the batched path.
+ * mats: host array of n_mats (1..4096).  Replaces earlier tables.
+ * Synchronises the stream.  PCC_E_INVALID on a bad spec or material. */
+int pcc_tables_build(pcc_ctx *ctx, const pcc_material *mats, int n_mats,
+                     const pcc_table_spec *spec, void *stream);
+
+/* Copy the FP64 tables to host arrays (any pointer may be NULL):
+ * brems_sigma[n_mats][n_rows], brems_cdf[n_mats][n_rows][n_cols], bh_sigma,
+ * bh_cdf (same shapes), tri_gp_cdf[n_rows][n_cols], tri_split_cdf, and
+ * screening[n_mats][8] = {L_TF, L_D, eta_TF, eta_D, I_TFD, L_R, f_C, Z}
+ * (lengths in units of hbar/(m_e c)).  Synchronous. */
+int pcc_tables_read(pcc_ctx *ctx, double *brems_sigma, double *brems_cdf, double *bh_sigma,
+                    double *bh_cdf, double *tri_gp_cdf, double *tri_split_cdf, double *screening);
+
+/* Bin by cell (Sec. III.A: "in a given mesh cell"): counting sort of `in`
+ * into the cell-region layout of `out`, each cell's particles in ascending
+ * pid order.  Region of cell c: count_c + max(slack_abs, ceil(slack_rel *
+ * count_c)) slots.  out->cell_start/cell_count/cell_added are written;
+ * cell_added is zeroed.  Synchronises the stream (it reads back the
+ * largest cell); PCC_E_CAPACITY if the regions do not fit out->capacity or
+ * a cell holds more than 16384 particles. */
+int pcc_bin(pcc_ctx *ctx, const pcc_particles *in, int n_cells, pcc_species *out,
+            int slack_abs, double slack_rel, void *stream);
+
+/* One collision step (Sec. III.A, Eq. proba1-proba3) over all cells:
+ * electron-ion pairs (Brems then Trident on each pair), positron-ion pairs,
+ * photon-ion pairs (Bethe-Heitler); N_pair = max(N_p, N_t) random pairs per
+ * cell, acceptance 1 - exp(-(n_p n_t / n_pt) sigma' p' c dt / (gamma gamma_i))
+ * then the weight correction W_t / max(W_p, W_t); inverse-CDF sampling of
+ * the secondary energy; secondaries appended to the cell regions (photons
+ * from Brems, e-/e+ from Trident and BH); absorbed photons removed.  ion may
+ * not be NULL; em, ep, ph may have zero live particles but not be NULL.
+ * precision PCC_FP64_PLAIN: one thread block per cell, FP64 arithmetic;
+ * PCC_FP32_BATCHED: persistent kernel, FP32 arithmetic.  ledger: optional
+ * device float[n_cells][4], per cell {radiated photon energy, compensation,
+ * created weight, compensation} accumulated with Kahan summation.
+ * Random numbers: Philox4x32-10 keyed by `seed`, counters (slot or pair,
+ * cell, step, stream tag).  Asynchronous. */
+int pcc_collide(pcc_ctx *ctx, const pcc_cells *cells, pcc_species *em, pcc_species *ep,
+                pcc_species *ph, const pcc_species *ion, double dt, uint64_t seed, uint64_t step,
+                unsigned process_mask, int precision, float *ledger, void *stream);
+
+/* Make the secondaries of the last step live (Sec. III.A: created
+ * macro-particles join the simulation): per cell, order the appended
+ * particles by pid, then cell_count += cell_added, cell_added = 0.
+ * Asynchronous. */
+int pcc_append_secondaries(pcc_ctx *ctx, int n_cells, pcc_species *sp, void *stream);
+
+/* Diagnostic: the pairing of Sec. III.A for one projectile species against
+ * the targets.  For live projectile slot s of cell c (written at index
+ * cell_start[c] + s): out_j = its first pair index j, out_t = that pair's
+ * target slot.  group 0 = electrons, 1 = positrons, 2 = photons.
+ * Asynchronous. */
+int pcc_pairing(pcc_ctx *ctx, int n_cells, const pcc_species *proj, const pcc_species *targ,
+                int group, uint64_t seed, uint64_t step, int *out_j, int *out_t, void *stream);
+
+/* FP64 totals over the live particles of a species (Sec. III.A energy
+ * bookkeeping): out[0] = sum W, out[1] = sum W E (E = gamma for leptons,
+ * k for photons, in m_e c^2), out[2] = sum W |u|.  out: device double[3].
+ * Deterministic for a given layout.  Asynchronous. */
+int pcc_totals(pcc_ctx *ctx, int n_cells, const pcc_species *sp, int is_photon, double *out,
+               void *stream);
+
+/* Read and clear the device status word and step counters.  Synchronises
+ * the stream.  status_out: PCC_ST_* bits; stats_out may be NULL. */
+int pcc_read_status(pcc_ctx *ctx, unsigned *status_out, pcc_stats *stats_out, void *stream);
+
+/* Expected-emission operator (rate form of Eq. N_br_theo1/2, radiative
+ * stopping power of Sec. III.B) per cell c for electrons at rest ions:
+ *   out[c][0] = n_i sum_s w_s v_s sigma_B(gamma_s)
+ *   out[c][1] = n_i sum_s w_s v_s sigma_T(gamma_s)
+ *   out[c][2] = n_i sum_s w_s v_s int k dsigma_B/dk dk
+ * with sigma_B = int_{1e-7}^{1} dsigma/dk (gamma-1) dx by a fixed n_quad
+ * point Gauss-Legendre rule in ln x, for parameters params[c][5] =
+ * {n_i, T_e, Zstar, s_TF, s_D} of element Z.  gamma, w: [n_cells][n_samples].
+ * All device float32.  n_quad <= 128.  Asynchronous. */
+int pcc_expected_emission_fwd(pcc_ctx *ctx, int n_cells, int n_samples, int Z, int n_quad,
+                              const float *params, const float *gamma, const float *w, float *out,
+                              void *stream);
+
+/* Adjoint of pcc_expected_emission_fwd: grad_params[c][k] = sum_j
+ * grad_out[c][j] d out[c][j] / d params[c][k].  The Debye-length lower bound
+ * max(lambda_D, r_i) takes the derivative of the active branch (r_i on a
+ * tie).  All device float32.  Asynchronous. */
+int pcc_expected_emission_bwd(pcc_ctx *ctx, int n_cells, int n_samples, int Z, int n_quad,
+                              const float *params, const float *gamma, const float *w,
+                              const float *grad_out, float *grad_params, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCC_H */

@@ -1,0 +1,92 @@
+// Context lifetime, status readback and error reporting of the C ABI.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "pcc_internal.h"
+
+namespace pcc {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return PCC_E_CUDA;
+}
+
+int ensure_scratch(pcc_ctx* ctx, size_t bytes)
+{
+    if (bytes <= ctx->scratch_bytes) return PCC_OK;
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->scratch, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+    ctx->scratch_bytes = bytes;
+    return PCC_OK;
+}
+
+}  // namespace pcc
+
+using namespace pcc;
+
+void pcc_free_tables(pcc_ctx* ctx);
+
+extern "C" const char* pcc_version(void) { return "pcc 0.1 (sm_103a)"; }
+
+extern "C" const char* pcc_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int pcc_create(pcc_ctx** out, int device)
+{
+    if (!out) { set_error("pcc_create: null output"); return PCC_E_INVALID; }
+    *out = nullptr;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "pcc_create: cudaSetDevice");
+    pcc_ctx* ctx = new pcc_ctx();
+    ctx->device = device;
+    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->stats, sizeof(DevStats));
+    if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, sizeof(DevStats));
+    if (e != cudaSuccess) {
+        if (ctx->stats) cudaFree(ctx->stats);
+        delete ctx;
+        return cuda_fail(e, "pcc_create");
+    }
+    *out = ctx;
+    return PCC_OK;
+}
+
+extern "C" void pcc_destroy(pcc_ctx* ctx)
+{
+    if (!ctx) return;
+    pcc_free_tables(ctx);
+    if (ctx->stats) cudaFree(ctx->stats);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    delete ctx;
+}
+
+extern "C" int pcc_read_status(pcc_ctx* ctx, unsigned* status_out, pcc_stats* stats_out, void* stream)
+{
+    if (!ctx) { set_error("pcc_read_status: null context"); return PCC_E_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream;
+    DevStats h;
+    cudaError_t e = cudaMemcpyAsync(&h, ctx->stats, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "pcc_read_status");
+    if (status_out) *status_out = h.status;
+    if (stats_out) {
+        for (int i = 0; i < 3; ++i) stats_out->pairs[i] = h.pairs[i];
+        for (int i = 0; i < 5; ++i) {
+            stats_out->accepted[i] = h.accepted[i];
+            stats_out->created[i] = h.created[i];
+        }
+        stats_out->energy_change = h.energy_change;
+        stats_out->charge_change = h.charge_change;
+    }
+    return PCC_OK;
+}

@@ -1,0 +1,55 @@
+// Library-internal context and launcher declarations (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/pcc.h"
+#include "pcc_device.cuh"
+
+struct pcc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    // tables (device)
+    int n_mat = 0;
+    pcc_table_spec spec{};
+    double* screen = nullptr;         // [n_mat][8]
+    double* brems_sigma = nullptr;    // [n_mat][R]
+    double* brems_cdf = nullptr;      // [n_mat][R][C]
+    double* bh_sigma = nullptr;
+    double* bh_cdf = nullptr;
+    double* tri_gp_cdf = nullptr;     // [R][C]
+    double* tri_split_cdf = nullptr;
+    float* f_brems_lnsig = nullptr;   // FP32 copies: ln sigma and CDFs
+    float* f_brems_cdf = nullptr;
+    float* f_bh_lnsig = nullptr;
+    float* f_bh_cdf = nullptr;
+    float* f_tri_gp_cdf = nullptr;
+    float* f_tri_split_cdf = nullptr;
+    float* f_Z = nullptr;             // [n_mat] nuclear charge as float
+    // status and counters
+    pcc::DevStats* stats = nullptr;
+    // scratch
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+namespace pcc {
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+int ensure_scratch(pcc_ctx* ctx, size_t bytes);
+
+// Table geometry passed to kernels by value.
+struct TableGeom {
+    int n_rows, n_cols;
+    double T_min, T_max;   // row variable range
+    double ln_T_min, inv_dln_row;
+    double ln_x_min;       // Brems column floor (log)
+    double ln_tri_min;     // Trident pair column floor (log)
+    float f_ln_T_min, f_inv_dln_row, f_ln_x_min, f_ln_tri_min;
+};
+TableGeom make_geom(const pcc_table_spec& s);
+
+}  // namespace pcc

@@ -1,0 +1,294 @@
+"""Thin ctypes binding of the C ABI in include/pcc.h.
+
+Argument marshalling only: every step of the collision path runs in the
+CUDA kernels of libpcc.so.  PyTorch tensors supply device memory and the
+current CUDA stream.  There is no CPU fallback: importing the compute
+functions without a built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpcc.so")
+
+PCC_OK, PCC_E_INVALID, PCC_E_CUDA, PCC_E_CAPACITY, PCC_E_NO_TABLES = 0, 1, 2, 3, 4
+ST_TABLE_RANGE, ST_PROB_LARGE, ST_CAPACITY, ST_NONFINITE, ST_ID_RANGE, ST_TIMEOUT = 1, 2, 4, 8, 16, 32
+FP64_PLAIN, FP32_BATCHED = 0, 1
+BREMS, TRIDENT, BH = 1, 2, 4
+GROUP_EM, GROUP_EP, GROUP_PH = 0x100, 0x200, 0x400
+
+_vp = C.c_void_p
+_fp = C.POINTER(C.c_float)
+
+
+class Material(C.Structure):
+    _fields_ = [("Z", C.c_int), ("Zstar", C.c_double), ("n_i", C.c_double), ("T_e", C.c_double),
+                ("s_TF", C.c_double), ("s_D", C.c_double)]
+
+
+class TableSpec(C.Structure):
+    _fields_ = [("n_rows", C.c_int), ("n_cols", C.c_int), ("quad_nodes", C.c_int), ("gamma_min", C.c_double),
+                ("gamma_max", C.c_double), ("cutoff_exp", C.c_int), ("tri_y_min", C.c_double),
+                ("nr_qbounds", C.c_int)]
+
+
+class Species(C.Structure):
+    _fields_ = [("ux", _vp), ("uy", _vp), ("uz", _vp), ("w", _vp), ("x", _vp), ("pid", _vp),
+                ("cell_start", _vp), ("cell_count", _vp), ("cell_added", _vp), ("capacity", C.c_int)]
+
+
+class Particles(C.Structure):
+    _fields_ = [("n", C.c_int), ("ux", _vp), ("uy", _vp), ("uz", _vp), ("w", _vp), ("x", _vp), ("pid", _vp),
+                ("cell", _vp)]
+
+
+class Cells(C.Structure):
+    _fields_ = [("n_cells", C.c_int), ("material_of_cell", _vp), ("ion_mass", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("pairs", C.c_ulonglong * 3), ("accepted", C.c_ulonglong * 5), ("created", C.c_ulonglong * 5),
+                ("energy_change", C.c_double), ("charge_change", C.c_double)]
+
+
+_lib = None
+
+EXPORTS = {
+    "pcc_version": (C.c_char_p, []),
+    "pcc_last_error": (C.c_char_p, []),
+    "pcc_create": (C.c_int, [C.POINTER(_vp), C.c_int]),
+    "pcc_destroy": (None, [_vp]),
+    "pcc_tables_build": (C.c_int, [_vp, C.POINTER(Material), C.c_int, C.POINTER(TableSpec), _vp]),
+    "pcc_tables_read": (C.c_int, [_vp] + [_vp] * 7),
+    "pcc_bin": (C.c_int, [_vp, C.POINTER(Particles), C.c_int, C.POINTER(Species), C.c_int, C.c_double, _vp]),
+    "pcc_collide": (C.c_int, [_vp, C.POINTER(Cells), C.POINTER(Species), C.POINTER(Species), C.POINTER(Species),
+                              C.POINTER(Species), C.c_double, C.c_uint64, C.c_uint64, C.c_uint, C.c_int, _vp, _vp]),
+    "pcc_append_secondaries": (C.c_int, [_vp, C.c_int, C.POINTER(Species), _vp]),
+    "pcc_pairing": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.POINTER(Species), C.c_int, C.c_uint64,
+                              C.c_uint64, _vp, _vp, _vp]),
+    "pcc_totals": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.c_int, _vp, _vp]),
+    "pcc_read_status": (C.c_int, [_vp, C.POINTER(C.c_uint), C.POINTER(Stats), _vp]),
+    "pcc_expected_emission_fwd": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "pcc_expected_emission_bwd": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp,
+                                            _vp]),
+}
+
+
+def load(path: str | None = None):
+    """Load libpcc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run paper_1907_02814_gb300.build.build() first")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PccError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc != PCC_OK:
+        msg = load().pcc_last_error().decode()
+        raise PccError(f"{what} failed with status {rc}: {msg}")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def material(Z, Zstar, n_i, T_e, s_TF=1.0, s_D=1.0) -> Material:
+    return Material(int(Z), float(Zstar), float(n_i), float(T_e), float(s_TF), float(s_D))
+
+
+def table_spec(n_rows=256, n_cols=256, quad_nodes=8, gamma_min=1.002, gamma_max=2000.0, cutoff_exp=7,
+               tri_y_min=1e-5, nr_qbounds=0) -> TableSpec:
+    return TableSpec(n_rows, n_cols, quad_nodes, gamma_min, gamma_max, cutoff_exp, tri_y_min, nr_qbounds)
+
+
+class Context:
+    """A library context on one CUDA device (tables, status, scratch)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        _check(self.lib.pcc_create(C.byref(h), int(device)), "pcc_create")
+        self.h = h
+        self.device = device
+        self.spec = None
+        self.n_mat = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pcc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tables_build(self, materials, spec: TableSpec | None = None, stream=None):
+        spec = spec or table_spec()
+        arr = (Material * len(materials))(*materials)
+        _check(self.lib.pcc_tables_build(self.h, arr, len(materials), C.byref(spec), _stream(stream)),
+               "pcc_tables_build")
+        self.spec = spec
+        self.n_mat = len(materials)
+
+    def tables_read(self):
+        R, Cn, M = self.spec.n_rows, self.spec.n_cols, self.n_mat
+        out = {"brems_sigma": np.zeros((M, R)), "brems_cdf": np.zeros((M, R, Cn)), "bh_sigma": np.zeros((M, R)),
+               "bh_cdf": np.zeros((M, R, Cn)), "tri_gp_cdf": np.zeros((R, Cn)), "tri_split_cdf": np.zeros((R, Cn)),
+               "screening": np.zeros((M, 8))}
+        keys = ["brems_sigma", "brems_cdf", "bh_sigma", "bh_cdf", "tri_gp_cdf", "tri_split_cdf", "screening"]
+        _check(self.lib.pcc_tables_read(self.h, *[C.c_void_p(out[k].ctypes.data) for k in keys]),
+               "pcc_tables_read")
+        return out
+
+    def read_status(self, stream=None):
+        st = C.c_uint(0)
+        s = Stats()
+        _check(self.lib.pcc_read_status(self.h, C.byref(st), C.byref(s), _stream(stream)), "pcc_read_status")
+        return st.value, {"pairs": list(s.pairs), "accepted": list(s.accepted), "created": list(s.created),
+                          "energy_change": s.energy_change, "charge_change": s.charge_change}
+
+
+@dataclass
+class DeviceSpecies:
+    """A species in cell-region layout held in torch tensors (device)."""
+    ux: object
+    uy: object
+    uz: object
+    w: object
+    pid: object            # int64 tensor holding the uint64 bit patterns
+    cell_start: object     # int32 [n_cells + 1]
+    cell_count: object     # int32 [n_cells]
+    cell_added: object     # int32 [n_cells]
+    x: object = None
+
+    @property
+    def capacity(self):
+        return int(self.w.numel())
+
+    @staticmethod
+    def empty(n_cells, capacity, device="cuda", with_x=False):
+        import torch
+        f = lambda: torch.zeros(capacity, dtype=torch.float32, device=device)
+        return DeviceSpecies(f(), f(), f(), f(), torch.zeros(capacity, dtype=torch.int64, device=device),
+                             torch.zeros(n_cells + 1, dtype=torch.int32, device=device),
+                             torch.zeros(n_cells, dtype=torch.int32, device=device),
+                             torch.zeros(n_cells, dtype=torch.int32, device=device),
+                             f() if with_x else None)
+
+    def cstruct(self) -> Species:
+        return Species(_ptr(self.ux), _ptr(self.uy), _ptr(self.uz), _ptr(self.w), _ptr(self.x), _ptr(self.pid),
+                       _ptr(self.cell_start), _ptr(self.cell_count), _ptr(self.cell_added), self.capacity)
+
+    def live_host(self):
+        """Live particles copied to the host in storage order (cell, pid)."""
+        start = self.cell_start.cpu().numpy()
+        count = self.cell_count.cpu().numpy()
+        n_cells = len(count)
+        idx = np.concatenate([np.arange(start[c], start[c] + count[c]) for c in range(n_cells)]) \
+            if n_cells else np.zeros(0, np.int64)
+        idx = idx.astype(np.int64)
+        out = {k: getattr(self, k).cpu().numpy()[idx] for k in ("ux", "uy", "uz", "w")}
+        out["pid"] = self.pid.cpu().numpy()[idx].view(np.uint64)
+        out["cell"] = np.repeat(np.arange(n_cells, dtype=np.int32), count)
+        out["x"] = self.x.cpu().numpy()[idx] if self.x is not None else None
+        return out
+
+
+def particles_to_device(d: dict, device="cuda"):
+    """Host particle dict (workloads format) -> device tensors for pcc_bin."""
+    import torch
+    t = {k: torch.as_tensor(np.ascontiguousarray(d[k]), device=device) for k in ("ux", "uy", "uz", "w")}
+    t["pid"] = torch.as_tensor(np.ascontiguousarray(d["pid"]).view(np.int64), device=device)
+    t["cell"] = torch.as_tensor(np.ascontiguousarray(d["cell"], dtype=np.int32), device=device)
+    t["x"] = torch.as_tensor(np.ascontiguousarray(d["x"]), device=device) if d.get("x") is not None else None
+    t["n"] = len(d["w"])
+    return t
+
+
+def bin(ctx: Context, parts: dict, n_cells: int, out: DeviceSpecies, slack_abs=8, slack_rel=0.25, stream=None):
+    p = Particles(int(parts["n"]), _ptr(parts["ux"]), _ptr(parts["uy"]), _ptr(parts["uz"]), _ptr(parts["w"]),
+                  _ptr(parts.get("x")), _ptr(parts["pid"]), _ptr(parts["cell"]))
+    s = out.cstruct()
+    _check(ctx.lib.pcc_bin(ctx.h, C.byref(p), int(n_cells), C.byref(s), int(slack_abs), float(slack_rel),
+                           _stream(stream)), "pcc_bin")
+
+
+def collide(ctx: Context, n_cells: int, material_of_cell, ion_mass: float, em: DeviceSpecies, ep: DeviceSpecies,
+            ph: DeviceSpecies, ion: DeviceSpecies, dt: float, seed: int, step: int, mask=BREMS | TRIDENT | BH,
+            precision=FP32_BATCHED, ledger=None, stream=None):
+    cells = Cells(int(n_cells), _ptr(material_of_cell), float(ion_mass))
+    s = [x.cstruct() for x in (em, ep, ph, ion)]
+    _check(ctx.lib.pcc_collide(ctx.h, C.byref(cells), C.byref(s[0]), C.byref(s[1]), C.byref(s[2]), C.byref(s[3]),
+                               float(dt), C.c_uint64(int(seed)), C.c_uint64(int(step)), int(mask), int(precision),
+                               _ptr(ledger), _stream(stream)), "pcc_collide")
+
+
+def append_secondaries(ctx: Context, n_cells: int, sp: DeviceSpecies, stream=None):
+    s = sp.cstruct()
+    _check(ctx.lib.pcc_append_secondaries(ctx.h, int(n_cells), C.byref(s), _stream(stream)),
+           "pcc_append_secondaries")
+
+
+def pairing(ctx: Context, n_cells, proj: DeviceSpecies, targ: DeviceSpecies, group, seed, step, stream=None):
+    import torch
+    oj = torch.full((proj.capacity,), -1, dtype=torch.int32, device=proj.w.device)
+    ot = torch.full((proj.capacity,), -1, dtype=torch.int32, device=proj.w.device)
+    a, b = proj.cstruct(), targ.cstruct()
+    _check(ctx.lib.pcc_pairing(ctx.h, int(n_cells), C.byref(a), C.byref(b), int(group), C.c_uint64(int(seed)),
+                               C.c_uint64(int(step)), _ptr(oj), _ptr(ot), _stream(stream)), "pcc_pairing")
+    return oj, ot
+
+
+def totals(ctx: Context, n_cells, sp: DeviceSpecies, is_photon=False, stream=None):
+    import torch
+    out = torch.zeros(3, dtype=torch.float64, device=sp.w.device)
+    s = sp.cstruct()
+    _check(ctx.lib.pcc_totals(ctx.h, int(n_cells), C.byref(s), int(bool(is_photon)), _ptr(out), _stream(stream)),
+           "pcc_totals")
+    return out
+
+
+def expected_emission_fwd(ctx: Context, Z, params, gamma, w, n_quad=64, stream=None):
+    import torch
+    n_cells, n_samples = gamma.shape
+    out = torch.empty((n_cells, 3), dtype=torch.float32, device=gamma.device)
+    _check(ctx.lib.pcc_expected_emission_fwd(ctx.h, n_cells, n_samples, int(Z), int(n_quad), _ptr(params),
+                                             _ptr(gamma), _ptr(w), _ptr(out), _stream(stream)),
+           "pcc_expected_emission_fwd")
+    return out
+
+
+def expected_emission_bwd(ctx: Context, Z, params, gamma, w, grad_out, n_quad=64, stream=None):
+    import torch
+    n_cells, n_samples = gamma.shape
+    g = torch.empty((n_cells, 5), dtype=torch.float32, device=gamma.device)
+    _check(ctx.lib.pcc_expected_emission_bwd(ctx.h, n_cells, n_samples, int(Z), int(n_quad), _ptr(params),
+                                             _ptr(gamma), _ptr(w), _ptr(grad_out.contiguous()), _ptr(g),
+                                             _stream(stream)), "pcc_expected_emission_bwd")
+    return g

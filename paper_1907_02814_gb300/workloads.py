@@ -271,3 +271,59 @@ def emission_params(n_cells=4096, n_samples=512, seed=5):
     T = 10.0 ** rng.uniform(np.log10(0.5), np.log10(200.0), (n_cells, n_samples)) / MEC2_MEV
     return {"n_i": n_i, "T_e": T_e, "Zstar": Zs, "s_TF": np.ones(n_cells), "s_D": np.ones(n_cells),
             "gamma": 1.0 + T, "w": np.ones((n_cells, n_samples)), "Z": 29}
+
+
+def batched_cu_device(counts, device="cuda", cells=None):
+    """Particles of the batched workload drawn on the device with a seeded
+    torch generator (same distributions as batched_cu_host, different
+    stream).  Returns {species: dict of tensors} with the cell-sorted,
+    pid-ascending order of a fresh draw; ``cells`` restricts to a subset."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(counts["seed"]) * 7919 + 17)
+    out = {}
+    spec = {"em": (counts["e"], "lepton"), "ion": (counts["i"], "ion"), "ph": (counts["g"], "photon")}
+    for name, (cnt, kind) in spec.items():
+        cnt_t = torch.as_tensor(cnt, dtype=torch.int64, device=device)
+        n = int(cnt_t.sum())
+        cell = torch.repeat_interleave(torch.arange(len(cnt), device=device, dtype=torch.int32), cnt_t)
+        pid = torch.arange(n, device=device, dtype=torch.int64)
+        if kind == "lepton":
+            u = torch.rand(n, device=device, generator=gen, dtype=torch.float64)
+            T = -torch.log1p(-u) * (1.0 / MEC2_MEV)
+            p = torch.sqrt(T * (T + 2.0))
+            w = torch.full((n,), counts["w_e"], device=device, dtype=torch.float32)
+        elif kind == "photon":
+            u = torch.rand(n, device=device, generator=gen, dtype=torch.float64)
+            p = 1.0 / (0.5 - u * (0.5 - 1.0 / 200.0))
+            w = torch.full((n,), counts["w_e"], device=device, dtype=torch.float32)
+        else:
+            sig = float(np.sqrt(counts["T_e"] / (counts["ion_mass"] * MEC2_MEV * 1e6)))
+            g3 = torch.randn((3, n), device=device, generator=gen, dtype=torch.float32) * sig
+            ni = torch.as_tensor(cnt, dtype=torch.float32, device=device).clamp_min(1.0)
+            w = (counts["n_i"] / ni)[cell.long()]
+            d = {"ux": g3[0].contiguous(), "uy": g3[1].contiguous(), "uz": g3[2].contiguous(), "w": w, "pid": pid,
+                 "cell": cell, "x": None, "n": n}
+            out[name] = d
+            continue
+        mu = torch.rand(n, device=device, generator=gen, dtype=torch.float64) * 2.0 - 1.0
+        phi = torch.rand(n, device=device, generator=gen, dtype=torch.float64) * (2.0 * np.pi)
+        s = torch.sqrt(1.0 - mu * mu)
+        d = {"ux": (p * s * torch.cos(phi)).float(), "uy": (p * s * torch.sin(phi)).float(),
+             "uz": (p * mu).float(), "w": w, "pid": pid, "cell": cell, "x": None, "n": n}
+        out[name] = d
+    if cells is not None:
+        keep_cells = torch.as_tensor(np.asarray(cells), device=device)
+        for name, d in out.items():
+            m = torch.isin(d["cell"], keep_cells.to(d["cell"].dtype))
+            out[name] = {k: (v[m] if torch.is_tensor(v) else v) for k, v in d.items()}
+            out[name]["n"] = int(m.sum())
+    return out
+
+
+def device_to_host(d):
+    """Tensor particle dict -> numpy dict in the workloads host format."""
+    h = {k: (v.cpu().numpy() if v is not None and not isinstance(v, int) else v) for k, v in d.items()}
+    h["pid"] = h["pid"].view(np.uint64)
+    h.pop("n", None)
+    return h

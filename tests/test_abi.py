@@ -1,0 +1,55 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports
+every function declared in include/pcc.h (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(pcc_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1907_02814_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("pcc_create", "pcc_tables_build", "pcc_bin", "pcc_collide", "pcc_append_secondaries",
+                 "pcc_read_status", "pcc_expected_emission_fwd", "pcc_expected_emission_bwd"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(lib):
+    from paper_1907_02814_gb300 import pcc
+    assert set(declared_functions()) == set(pcc.EXPORTS)
+    pcc.load()
+    assert pcc.load().pcc_version().decode().startswith("pcc")
+
+
+def test_null_arguments_rejected_without_a_device(lib):
+    from paper_1907_02814_gb300 import pcc
+    L = pcc.load()
+    assert L.pcc_create(None, 0) == pcc.PCC_E_INVALID
+    assert L.pcc_tables_build(None, None, 0, None, None) == pcc.PCC_E_INVALID
+    assert L.pcc_collide(None, None, None, None, None, None, 1.0, 0, 0, 7, 0, None, None) == pcc.PCC_E_INVALID
+    assert b"invalid" in L.pcc_last_error()
