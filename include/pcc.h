@@ -125,6 +125,8 @@ typedef struct {
     unsigned long long created[5];   /* events kept by the weight correction          */
     double energy_change;            /* sum over events of W (E_out - E_in), m_e c^2 m^-3 */
     double charge_change;            /* sum over events of W (q_out - q_in), e m^-3        */
+    unsigned long long candidates[3];/* batched path: pairs whose uniform fell below the
+                                        per-material bound and were evaluated in full    */
 } pcc_stats;
 
 /* Library version string and the message of the last synchronous error
@@ -178,7 +180,10 @@ int pcc_bin(pcc_ctx *ctx, const pcc_particles *in, int n_cells, pcc_species *out
  * from Brems, e-/e+ from Trident and BH); absorbed photons removed.  ion may
  * not be NULL; em, ep, ph may have zero live particles but not be NULL.
  * precision PCC_FP64_PLAIN: one thread block per cell, FP64 arithmetic;
- * PCC_FP32_BATCHED: persistent kernel, FP32 arithmetic.  ledger: optional
+ * PCC_FP32_BATCHED: persistent kernel, FP32 arithmetic, and a pair whose
+ * uniform is at or above a per-material bound of its acceptance probability
+ * is rejected without being evaluated (exact, since 1 - exp(-x) <= x; the
+ * Trident bound assumes ion-frame Lorentz factors below 1e7).  ledger: optional
  * device float[n_cells][4], per cell {radiated photon energy, compensation,
  * created weight, compensation} accumulated with Kahan summation.
  * Random numbers: Philox4x32-10 keyed by `seed`, counters (slot or pair,
@@ -186,6 +191,15 @@ int pcc_bin(pcc_ctx *ctx, const pcc_particles *in, int n_cells, pcc_species *out
 int pcc_collide(pcc_ctx *ctx, const pcc_cells *cells, pcc_species *em, pcc_species *ep,
                 pcc_species *ph, const pcc_species *ion, double dt, uint64_t seed, uint64_t step,
                 unsigned process_mask, int precision, float *ledger, void *stream);
+
+/* Launch schedule of the batched FP32 collision kernels (no counterpart in
+ * the paper; a performance setting that never changes results).  Cells are
+ * processed one per warp, largest size class first; min_blocks_per_sm
+ * (2, 3 or 4) selects the register budget of the kernel (a minimum of that
+ * many resident 256-thread blocks per SM) and blocks_per_sm caps the
+ * persistent grid (0 = as many as fit).  Applies to later pcc_collide calls
+ * on this context.  PCC_E_INVALID outside these ranges. */
+int pcc_set_schedule(pcc_ctx *ctx, int min_blocks_per_sm, int blocks_per_sm);
 
 /* Make the secondaries of the last step live (Sec. III.A: created
  * macro-particles join the simulation): per cell, order the appended

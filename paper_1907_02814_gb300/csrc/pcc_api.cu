@@ -65,6 +65,9 @@ extern "C" void pcc_destroy(pcc_ctx* ctx)
     pcc_free_tables(ctx);
     if (ctx->stats) cudaFree(ctx->stats);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->lists) cudaFree(ctx->lists);
+    if (ctx->queue_a) cudaFree(ctx->queue_a);
+    if (ctx->queue_b) cudaFree(ctx->queue_b);
     delete ctx;
 }
 
@@ -87,6 +90,7 @@ extern "C" int pcc_read_status(pcc_ctx* ctx, unsigned* status_out, pcc_stats* st
         }
         stats_out->energy_change = h.energy_change;
         stats_out->charge_change = h.charge_change;
+        for (int i = 0; i < 3; ++i) stats_out->candidates[i] = h.candidates[i];
     }
     return PCC_OK;
 }

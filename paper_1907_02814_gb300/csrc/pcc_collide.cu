@@ -40,18 +40,22 @@ struct StepArgs {
     const double *brems_sigma, *brems_cdf, *bh_sigma, *bh_cdf, *tri_gp, *tri_split, *screen;
     // FP32 tables
     const float *f_brems_lnsig, *f_brems_cdf, *f_bh_lnsig, *f_bh_cdf, *f_tri_gp, *f_tri_split, *f_Z;
+    const float* f_bound;    // [n_mat][3] acceptance bounds (Brems, Trident, BH)
     DevStats* st;
+    PhiloxKeys keys;         // round keys of the seed
+    float f_cdt;             // c dt in float
 };
 
 // ---- per-thread accumulators ---------------------------------------------
 struct Acc {
     unsigned long long pairs[3];
     unsigned accepted[5], created[5];
+    unsigned candidates[3];
     double dE, dQ;
     unsigned status;
     __device__ void zero()
     {
-        for (int i = 0; i < 3; ++i) pairs[i] = 0;
+        for (int i = 0; i < 3; ++i) pairs[i] = 0, candidates[i] = 0;
         for (int i = 0; i < 5; ++i) accepted[i] = created[i] = 0;
         dE = dQ = 0.0;
         status = 0;
@@ -65,6 +69,16 @@ struct WarpGroup {
     __device__ int size() const { return 32; }
     __device__ void sync() const { __syncwarp(); }
     template <typename T> __device__ T sum(T v) const { return warp_sum(v); }
+    __device__ float fmin(float v) const
+    {
+        for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
+    __device__ float fmax(float v) const
+    {
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
     __device__ bool any(bool p) const { return __any_sync(0xffffffffu, p); }
 };
 
@@ -85,6 +99,18 @@ struct CtaGroup {
         for (int k = 0; k < nw; ++k) t += (T)red[k];
         return t;
     }
+    __device__ float fmin(float v) const { return -fmax(-v); }
+    __device__ float fmax(float v) const
+    {
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[w] = (double)v;
+        __syncthreads();
+        float t = (float)red[0];
+        for (int k = 1; k < nw; ++k) t = fmaxf(t, (float)red[k]);
+        return t;
+    }
     __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
 };
 
@@ -99,6 +125,21 @@ template <> struct Tab<float> {
     const float *bsig, *bcdf, *hsig, *hcdf, *tgp, *tsp;   // bsig/hsig hold ln sigma
     __device__ float ln_sigma(const float* s, int i) const { return s[i]; }
 };
+
+// Arithmetic of the two paths: FP64 plain uses correctly rounded library
+// functions; the FP32 batched path uses the hardware approximations (a few
+// ulp), which changes an accept decision only for pairs within ~1e-6 of the
+// threshold.
+__device__ __forceinline__ double q_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float q_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double q_log(double a) { return log(a); }
+__device__ __forceinline__ float q_log(float a) { return __logf(a); }
+__device__ __forceinline__ double q_exp(double a) { return exp(a); }
+__device__ __forceinline__ float q_exp(float a) { return __expf(a); }
+__device__ __forceinline__ double q_sqrt1(double a) { return sqrt(a); }            // a >= 1
+__device__ __forceinline__ float q_sqrt1(float a) { return a * rsqrtf(a); }        // a >= 1
+__device__ __forceinline__ double q_sqrt0(double a) { return sqrt(a); }            // a >= 0
+__device__ __forceinline__ float q_sqrt0(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
 
 template <typename Real>
 __device__ __forceinline__ Real row_ln0(const TableGeom& g);
@@ -116,15 +157,16 @@ __device__ __forceinline__ Real sigma_at(const Tab<Real>& tb, const Real* row_ta
                                          unsigned& status)
 {
     if (!(r >= (Real)g.T_min)) return (Real)0;
-    const Real t = (log(r) - row_ln0<Real>(g)) * row_inv<Real>(g);
+    const Real t = (q_log(r) - row_ln0<Real>(g)) * row_inv<Real>(g);
     if (t > (Real)(g.n_rows - 1)) {
         status |= PCC_ST_TABLE_RANGE;
-        return exp(tb.ln_sigma(row_tab, g.n_rows - 1));
+        return q_exp(tb.ln_sigma(row_tab, g.n_rows - 1));
     }
     int j = (int)t;
     if (j > g.n_rows - 2) j = g.n_rows - 2;
     const Real f = t - (Real)j;
-    return exp(((Real)1 - f) * tb.ln_sigma(row_tab, j) + f * tb.ln_sigma(row_tab, j + 1));
+    const Real l0 = tb.ln_sigma(row_tab, j), l1 = tb.ln_sigma(row_tab, j + 1);
+    return q_exp(l0 + f * (l1 - l0));
 }
 
 // Inverse-CDF sample of the column variable: stochastic row pick, binary
@@ -160,22 +202,27 @@ struct Frame {
     Real ui[3], gi;     // ion proper velocity and Lorentz factor
     Real gl;            // projectile energy in the simulation frame
     Real pp, Tp;        // momentum and kinetic energy in the ion frame
-    Real n[3];          // direction in the ion frame
+    Real n[3];          // ion-frame momentum; a unit direction after normalize()
+    __device__ __forceinline__ void normalize()
+    {
+        const Real inv = pp > (Real)0 ? (Real)1 / pp : (Real)0;
+        n[0] *= inv; n[1] *= inv; n[2] *= inv;
+    }
 };
 
 // E' = gi E - ui.p ; p' = p + ((ui.p)/(gi+1) - E) ui  (Sec. III.A transform)
 template <typename Real>
 __device__ __forceinline__ void to_ion_frame(Frame<Real>& f, const Real u[3])
 {
-    f.gl = sqrt((Real)1 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    f.gl = q_sqrt1((Real)1 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     const Real d = f.ui[0] * u[0] + f.ui[1] * u[1] + f.ui[2] * u[2];
-    const Real fac = d / (f.gi + (Real)1) - f.gl;
-    const Real px = u[0] + fac * f.ui[0], py = u[1] + fac * f.ui[1], pz = u[2] + fac * f.ui[2];
-    const Real p2 = px * px + py * py + pz * pz;
-    f.pp = sqrt(p2);
-    f.Tp = p2 / ((Real)1 + sqrt((Real)1 + p2));
-    const Real inv = f.pp > (Real)0 ? (Real)1 / f.pp : (Real)0;
-    f.n[0] = px * inv; f.n[1] = py * inv; f.n[2] = pz * inv;
+    const Real fac = q_div(d, f.gi + (Real)1) - f.gl;
+    f.n[0] = u[0] + fac * f.ui[0];
+    f.n[1] = u[1] + fac * f.ui[1];
+    f.n[2] = u[2] + fac * f.ui[2];
+    const Real p2 = f.n[0] * f.n[0] + f.n[1] * f.n[1] + f.n[2] * f.n[2];
+    f.pp = q_sqrt0(p2);
+    f.Tp = q_div(p2, (Real)1 + q_sqrt1((Real)1 + p2));
 }
 
 // (E', p') in the ion frame back to the simulation frame.
@@ -264,101 +311,219 @@ __device__ __forceinline__ Pairing make_pairing(const G& grp, uint32_t Np, uint3
     return P;
 }
 
+// ---- rare event paths (out of line: they run on about 1e-4 of the pairs) -----
+struct EventResult {
+    float u[3];        // projectile after the event (lab frame)
+    double dE;         // W (E_out - E_in)
+    float rad, wc;     // radiated photon energy W k, created weight
+    unsigned status;
+    int created;       // 1 when the weight correction kept the event
+};
+
+// Brems event on pair j (Sec. III.A): weight correction, inverse-CDF photon
+// energy, photon parallel to the electron in the ion frame, recoil.
+template <typename Real>
+__device__ __noinline__ EventResult brems_event(const StepArgs* ap, Tab<Real> tb, int group, int cell, int mat,
+                                                uint32_t j, float wp, float wt, float xpos, Frame<Real> f)
+{
+    const StepArgs& a = *ap;
+    EventResult r{};
+    f.normalize();
+    const int ch = group == kGroupEm ? kChBremsEm : kChBremsEp;
+    const Philox4 ev = draw(j, cell, a.step, stream_tag(group, kEvtBrems, 0), a.seed);
+    if ((wt < wp) && !(u01<Real>(ev.v[0]) < (Real)wt / (Real)wp)) return r;
+    r.created = 1;
+    const Real* cdf = tb.bcdf + (size_t)mat * a.g.n_rows * a.g.n_cols;
+    const Real xk = sample_col<Real>(cdf, a.g, f.Tp, u01<Real>(ev.v[1]), u01<Real>(ev.v[2]), true, a.g.ln_x_min);
+    const Real kp = xk * f.Tp;
+    Real ue[3], kg[3], Ek;
+    const Real Ee = lepton_to_lab(f, f.Tp * ((Real)1 - xk), ue);
+    const Real pk[3] = {kp * f.n[0], kp * f.n[1], kp * f.n[2]};
+    from_ion_frame(f, kp, pk, Ek, kg);
+    const float gk[3] = {(float)kg[0], (float)kg[1], (float)kg[2]};
+    r.u[0] = (float)ue[0]; r.u[1] = (float)ue[1]; r.u[2] = (float)ue[2];
+    if (append_particle(a.ph, cell, gk, wp, xpos, a.em.x != nullptr, secondary_pid(a.step, ch, cell, j, 0),
+                        r.status)) {
+        r.dE = (double)wp * ((double)Ee + (double)Ek - (double)f.gl);
+        r.rad = wp * (float)Ek;
+        r.wc = wp;
+    }
+    return r;
+}
+
+// Trident event on pair j (Sec. II.D): pair energy from its CDF, positron
+// share from the split CDF, both leptons along the electron in the ion frame.
+template <typename Real>
+__device__ __noinline__ EventResult trident_event(const StepArgs* ap, Tab<Real> tb, int group, int cell, uint32_t j,
+                                                  float wp, float wt, float xpos, Frame<Real> f)
+{
+    const StepArgs& a = *ap;
+    EventResult r{};
+    f.normalize();
+    const int ch = group == kGroupEm ? kChTriEm : kChTriEp;
+    const Philox4 e1 = draw(j, cell, a.step, stream_tag(group, kEvtTri1, 0), a.seed);
+    if ((wt < wp) && !(u01<Real>(e1.v[0]) < (Real)wt / (Real)wp)) return r;
+    r.created = 1;
+    const Philox4 e2 = draw(j, cell, a.step, stream_tag(group, kEvtTri2, 0), a.seed);
+    const Real y = sample_col<Real>(tb.tgp, a.g, f.Tp - (Real)2, u01<Real>(e1.v[1]), u01<Real>(e1.v[2]), true,
+                                    a.g.ln_tri_min);
+    const Real gpair = (Real)2 + y * (f.Tp - (Real)2);
+    const Real y2 = sample_col<Real>(tb.tsp, a.g, gpair - (Real)2, u01<Real>(e1.v[3]), u01<Real>(e2.v[0]), false,
+                                     0.0);
+    Real uf[3], up[3], um[3];
+    const Real Ef = lepton_to_lab(f, (f.Tp - (Real)2) * ((Real)1 - y), uf);
+    const Real Ep = lepton_to_lab(f, y2 * (gpair - (Real)2), up);
+    const Real Em = lepton_to_lab(f, (gpair - (Real)2) * ((Real)1 - y2), um);
+    const float fm[3] = {(float)um[0], (float)um[1], (float)um[2]};
+    const float fp[3] = {(float)up[0], (float)up[1], (float)up[2]};
+    const bool hx = a.em.x != nullptr;
+    const bool ok1 = append_particle(a.em, cell, fm, wp, xpos, hx, secondary_pid(a.step, ch, cell, j, 0), r.status);
+    const bool ok2 = append_particle(a.ep, cell, fp, wp, xpos, hx, secondary_pid(a.step, ch, cell, j, 1), r.status);
+    if (ok1 && ok2) {
+        r.dE = (double)wp * ((double)Ef + (double)Ep + (double)Em - (double)f.gl);
+        r.wc = 2.f * wp;
+    }
+    r.u[0] = (float)uf[0]; r.u[1] = (float)uf[1]; r.u[2] = (float)uf[2];
+    return r;
+}
+
+// Bethe-Heitler event on pair j (Sec. III.A): e+ e- along the photon in the
+// ion frame, energies from the BH CDF; the photon is absorbed.
+template <typename Real>
+__device__ __noinline__ EventResult bh_event(const StepArgs* ap, Tab<Real> tb, int cell, int mat, uint32_t j, float wp,
+                                             float wt, float xpos, Frame<Real> f, Real kp, Real k)
+{
+    const StepArgs& a = *ap;
+    EventResult r{};
+    const Philox4 ev = draw(j, cell, a.step, stream_tag(kGroupPh, kEvtBH, 0), a.seed);
+    if ((wt < wp) && !(u01<Real>(ev.v[0]) < (Real)wt / (Real)wp)) return r;
+    r.created = 1;
+    const Real* cdf = tb.hcdf + (size_t)mat * a.g.n_rows * a.g.n_cols;
+    const Real y = sample_col<Real>(cdf, a.g, kp - (Real)2, u01<Real>(ev.v[1]), u01<Real>(ev.v[2]), false, 0.0);
+    Real up[3], um[3];
+    const Real Ep = lepton_to_lab(f, y * (kp - (Real)2), up);
+    const Real Em = lepton_to_lab(f, (kp - (Real)2) * ((Real)1 - y), um);
+    const float fm[3] = {(float)um[0], (float)um[1], (float)um[2]};
+    const float fp[3] = {(float)up[0], (float)up[1], (float)up[2]};
+    const bool hx = a.ph.x != nullptr;
+    const bool ok1 = append_particle(a.em, cell, fm, wp, xpos, hx, secondary_pid(a.step, kChBH, cell, j, 0), r.status);
+    const bool ok2 = append_particle(a.ep, cell, fp, wp, xpos, hx, secondary_pid(a.step, kChBH, cell, j, 1), r.status);
+    if (ok1 && ok2) {
+        r.dE = (double)wp * ((double)Ep + (double)Em - (double)k);
+        r.wc = 2.f * wp;
+    }
+    return r;
+}
+
 // ---- one electron/positron - ion pair: Brems then Trident -------------------
 template <typename Real>
-__device__ void ei_pair(const StepArgs& a, const Tab<Real>& tb, int group, int cell, int mat, Real Zf, Real coef,
-                        float u[3], float wp, float xpos, const SpeciesView& ion, int t_slot, uint32_t j, Real UB,
-                        Real UT, Acc& acc, Kahan& rad, Kahan& wcre, bool& had)
+__device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb, int group, int cell, int mat, Real Zf,
+                                        Real coef, float u[3], float wp, float xpos, int t_slot, uint32_t j, Real UB,
+                                        Real UT, Acc& acc, float& rad, float& wcre, bool& had)
 {
+    const StepArgs& a = *ap;
+    const SpeciesView& ion = a.ion;
     Frame<Real> f;
     f.ui[0] = ion.ux[t_slot]; f.ui[1] = ion.uy[t_slot]; f.ui[2] = ion.uz[t_slot];
-    const float wt = ion.w[t_slot];
-    f.gi = sqrt((Real)1 + f.ui[0] * f.ui[0] + f.ui[1] * f.ui[1] + f.ui[2] * f.ui[2]);
-    Real uu[3] = {(Real)u[0], (Real)u[1], (Real)u[2]};
+    f.gi = q_sqrt1((Real)1 + f.ui[0] * f.ui[0] + f.ui[1] * f.ui[1] + f.ui[2] * f.ui[2]);
+    const Real uu[3] = {(Real)u[0], (Real)u[1], (Real)u[2]};
     to_ion_frame(f, uu);
     if (!isfinite(f.gl)) { acc.status |= PCC_ST_NONFINITE; return; }
-    const SpeciesView& ph = a.ph;
-    const bool has_x = a.em.x != nullptr;
     if (a.mask & PCC_BREMS) {
-        const Real* row_tab = tb.bsig + (size_t)mat * a.g.n_rows;
-        const Real sig = sigma_at<Real>(tb, row_tab, a.g, f.Tp, acc.status);
-        if (sig > (Real)0) {
-            const Real x = coef * sig * f.pp / (f.gl * f.gi);
-            if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
-            if (UB < x && UB < -expm1(-x)) {
-                const int ch = group == kGroupEm ? kChBremsEm : kChBremsEp;
-                acc.accepted[ch]++;
-                const Philox4 ev = draw(j, cell, a.step, stream_tag(group, kEvtBrems, 0), a.seed);
-                if (!(wt < wp) || u01<Real>(ev.v[0]) < (Real)wt / (Real)wp) {
-                    acc.created[ch]++;
-                    const Real* cdf = tb.bcdf + (size_t)mat * a.g.n_rows * a.g.n_cols;
-                    const Real xk = sample_col<Real>(cdf, a.g, f.Tp, u01<Real>(ev.v[1]), u01<Real>(ev.v[2]), true,
-                                                     a.g.ln_x_min);
-                    const Real kp = xk * f.Tp;
-                    Real ue[3], kg[3], Ee, Ek;
-                    Ee = lepton_to_lab(f, f.Tp * ((Real)1 - xk), ue);
-                    const Real pk[3] = {kp * f.n[0], kp * f.n[1], kp * f.n[2]};
-                    from_ion_frame(f, kp, pk, Ek, kg);
-                    const float nu[3] = {(float)ue[0], (float)ue[1], (float)ue[2]};
-                    const float gk[3] = {(float)kg[0], (float)kg[1], (float)kg[2]};
-                    if (append_particle(ph, cell, gk, wp, xpos, has_x, secondary_pid(a.step, ch, cell, j, 0),
-                                        acc.status)) {
-                        acc.dE += (double)wp * ((double)Ee + (double)Ek - (double)f.gl);
-                        rad.add(wp * (float)Ek);
-                        wcre.add(wp);
-                        had = true;
-                    }
-                    u[0] = nu[0]; u[1] = nu[1]; u[2] = nu[2];
-                    uu[0] = nu[0]; uu[1] = nu[1]; uu[2] = nu[2];
-                    to_ion_frame(f, uu);
-                }
+        const Real sig = sigma_at<Real>(tb, tb.bsig + (size_t)mat * a.g.n_rows, a.g, f.Tp, acc.status);
+        const Real x = q_div(coef * sig * f.pp, f.gl * f.gi);
+        if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
+        if (sig > (Real)0 && UB < x && UB < -expm1(-x)) {
+            const int ch = group == kGroupEm ? kChBremsEm : kChBremsEp;
+            acc.accepted[ch]++;
+            const EventResult r = brems_event<Real>(ap, tb, group, cell, mat, j, wp, ion.w[t_slot], xpos, f);
+            if (r.created) {
+                acc.created[ch]++;
+                acc.dE += r.dE;
+                acc.status |= r.status;
+                rad += r.rad;
+                wcre += r.wc;
+                had = true;   // the projectile changed
+                u[0] = r.u[0]; u[1] = r.u[1]; u[2] = r.u[2];
+                const Real nu[3] = {(Real)u[0], (Real)u[1], (Real)u[2]};
+                to_ion_frame(f, nu);
             }
         }
     }
-    if (a.mask & PCC_TRIDENT) {
-        const Real g1 = (Real)1 + f.Tp;
-        const Real sig = sigma_trident<Real>(Zf, g1);
-        if (sig > (Real)0) {
-            const Real x = coef * sig * f.pp / (f.gl * f.gi);
-            if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
-            if (UT < x && UT < -expm1(-x)) {
-                const int ch = group == kGroupEm ? kChTriEm : kChTriEp;
-                acc.accepted[ch]++;
-                const Philox4 e1 = draw(j, cell, a.step, stream_tag(group, kEvtTri1, 0), a.seed);
-                if (!(wt < wp) || u01<Real>(e1.v[0]) < (Real)wt / (Real)wp) {
-                    acc.created[ch]++;
-                    const Philox4 e2 = draw(j, cell, a.step, stream_tag(group, kEvtTri2, 0), a.seed);
-                    const Real y = sample_col<Real>(tb.tgp, a.g, f.Tp - (Real)2, u01<Real>(e1.v[1]),
-                                                    u01<Real>(e1.v[2]), true, a.g.ln_tri_min);
-                    const Real gpair = (Real)2 + y * (f.Tp - (Real)2);
-                    const Real y2 = sample_col<Real>(tb.tsp, a.g, gpair - (Real)2, u01<Real>(e1.v[3]),
-                                                     u01<Real>(e2.v[0]), false, 0.0);
-                    Real uf[3], up[3], um[3];
-                    const Real Ef = lepton_to_lab(f, (f.Tp - (Real)2) * ((Real)1 - y), uf);
-                    const Real Ep = lepton_to_lab(f, y2 * (gpair - (Real)2), up);
-                    const Real Em = lepton_to_lab(f, (gpair - (Real)2) * ((Real)1 - y2), um);
-                    const float fm[3] = {(float)um[0], (float)um[1], (float)um[2]};
-                    const float fp[3] = {(float)up[0], (float)up[1], (float)up[2]};
-                    const bool ok1 = append_particle(a.em, cell, fm, wp, xpos, has_x,
-                                                     secondary_pid(a.step, ch, cell, j, 0), acc.status);
-                    const bool ok2 = append_particle(a.ep, cell, fp, wp, xpos, has_x,
-                                                     secondary_pid(a.step, ch, cell, j, 1), acc.status);
-                    if (ok1 && ok2) {
-                        acc.dE += (double)wp * ((double)Ef + (double)Ep + (double)Em - (double)f.gl);
-                        wcre.add(2.f * wp);
-                        had = true;
-                    }
-                    u[0] = (float)uf[0]; u[1] = (float)uf[1]; u[2] = (float)uf[2];
-                }
+    if ((a.mask & PCC_TRIDENT) && f.Tp >= (Real)2) {
+        // Gryaznykh fit (Sec. II.D) above the threshold gamma = 3
+        const Real l = q_log(q_div(f.Tp + (Real)5.5, (Real)6.89));
+        const Real sig = (Real)5.22e-34 * Zf * Zf * l * l * l;
+        const Real x = q_div(coef * sig * f.pp, f.gl * f.gi);
+        if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
+        if (sig > (Real)0 && UT < x && UT < -expm1(-x)) {
+            const int ch = group == kGroupEm ? kChTriEm : kChTriEp;
+            acc.accepted[ch]++;
+            const EventResult r = trident_event<Real>(ap, tb, group, cell, j, wp, ion.w[t_slot], xpos, f);
+            if (r.created) {
+                acc.created[ch]++;
+                acc.dE += r.dE;
+                acc.status |= r.status;
+                wcre += r.wc;
+                had = true;
+                u[0] = r.u[0]; u[1] = r.u[1]; u[2] = r.u[2];
             }
         }
     }
 }
 
+// Cell sums of Sec. III.A: n_p = sum W_p, n_t = sum W_t and
+// n_pt = sum over pairs of min(W_p, W_t).  One pass over both lists; when
+// every target of the cell has the same weight, a projectile's pairs all
+// contribute min(W_p, W_t), so n_pt needs no permutation.
+template <typename Real, class G>
+__device__ __forceinline__ void cell_sums(const G& grp, const SpeciesView& P, const SpeciesView& I, int p0, int t0,
+                                          uint32_t Np, uint32_t Nt, const Pairing& pr, Real& n_p, Real& n_t,
+                                          Real& n_pt)
+{
+    const float w0 = I.w[t0];
+    Real sp = 0, st = 0, sf = 0;
+    float wmin = w0, wmax = w0;
+    const uint32_t N = Np > Nt ? Np : Nt;
+#pragma unroll 4
+    for (uint32_t s = grp.rank(); s < N; s += grp.size()) {
+        if (s < Nt) {
+            const float wt = I.w[t0 + s];
+            st += (Real)wt;
+            wmin = fminf(wmin, wt);
+            wmax = fmaxf(wmax, wt);
+        }
+        if (s < Np) {
+            const float wp = P.w[p0 + s];
+            sp += (Real)wp;
+            const uint32_t npairs = pr.caseA ? 1u : (Nt - s + Np - 1) / Np;
+            sf += (Real)fminf(wp, w0) * (Real)npairs;
+        }
+    }
+    n_p = grp.sum(sp);
+    n_t = grp.sum(st);
+    const float lo = grp.fmin(wmin), hi = grp.fmax(wmax);
+    if (lo == hi) {
+        n_pt = grp.sum(sf);
+        return;
+    }
+    Real spt = 0;
+    for (uint32_t s = grp.rank(); s < Np; s += grp.size()) {
+        const float wp = P.w[p0 + s];
+        if (pr.caseA) {
+            spt += (Real)fminf(wp, I.w[t0 + pr.pair_of_slot(s) % Nt]);
+        } else {
+            for (uint32_t j = s; j < Nt; j += Np) spt += (Real)fminf(wp, I.w[t0 + pr.target_of_pair(j)]);
+        }
+    }
+    n_pt = grp.sum(spt);
+}
+
 // ---- one cell of electron (or positron) - ion pairs ---------------------------
 template <typename Real, class G>
-__device__ void ei_cell(const G& grp, const StepArgs& a, const Tab<Real>& tb, int group, int cell, Acc& acc)
+__device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, int group, int cell, Acc& acc)
 {
+    const StepArgs& a = *ap;
     const SpeciesView& P = group == kGroupEm ? a.em : a.ep;
     const SpeciesView& I = a.ion;
     const uint32_t Np = P.count[cell], Nt = I.count[cell];
@@ -369,74 +534,59 @@ __device__ void ei_cell(const G& grp, const StepArgs& a, const Tab<Real>& tb, in
         acc.status |= PCC_ST_NONFINITE;
         return;
     }
-    Real sp = 0, st = 0;
-    for (int s = grp.rank(); s < (int)Np; s += grp.size()) sp += (Real)P.w[p0 + s];
-    for (int s = grp.rank(); s < (int)Nt; s += grp.size()) st += (Real)I.w[t0 + s];
-    const Real n_p = grp.sum(sp), n_t = grp.sum(st);
     const Pairing pr = make_pairing(grp, Np, Nt, cell, group, a);
-    Real spt = 0;
-    for (int s = grp.rank(); s < (int)Np; s += grp.size()) {
-        const float wp = P.w[p0 + s];
-        if (pr.caseA) {
-            const uint32_t j = pr.pair_of_slot(s);
-            spt += (Real)fminf(wp, I.w[t0 + j % Nt]);
-        } else {
-            for (uint32_t j = s; j < Nt; j += Np) spt += (Real)fminf(wp, I.w[t0 + pr.target_of_pair(j)]);
-        }
-    }
-    const Real n_pt = grp.sum(spt);
+    Real n_p, n_t, n_pt;
+    cell_sums<Real>(grp, P, I, p0, t0, Np, Nt, pr, n_p, n_t, n_pt);
     const Real coef = (n_p / n_pt) * n_t * (Real)(kC * a.dt);
     const uint32_t Npair = Np > Nt ? Np : Nt;
     if (grp.rank() == 0) acc.pairs[group] += Npair;
     if (Npair > 65536u || (uint32_t)cell > 0xFFFFFFu || a.step > 0x7FFFFull) acc.status |= PCC_ST_ID_RANGE;
     const Real Zf = sizeof(Real) == 8 ? (Real)a.screen[(size_t)mat * kScreenFields + 7] : (Real)a.f_Z[mat];
-    Kahan rad, wcre;
+    // the batched FP32 path rejects from the uniform alone below the bounds
+    const bool quick = sizeof(Real) == 4;
+    const Real bB = quick && (a.mask & PCC_BREMS) ? coef * (Real)a.f_bound[3 * mat] : (Real)0;
+    const Real bT = quick && (a.mask & PCC_TRIDENT) ? coef * (Real)a.f_bound[3 * mat + 1] : (Real)0;
+    float rad = 0.f, wcre = 0.f;
     bool had = false;
     const bool has_x = P.x != nullptr;
     for (uint32_t q = grp.rank(); 2 * q < Np; q += grp.size()) {
         const int nh = (2 * q + 1 < Np) ? 2 : 1;
-        float u[2][3], w[2], xp[2];
-        bool dirty[2] = {false, false};
+        // case A: one pair per projectile, one Philox draw serves both slots
+        Philox4 ac{};
+        if (pr.caseA) ac = draw(q, cell, a.step, stream_tag(group, kAccept, 0), a.seed);
         for (int h = 0; h < nh; ++h) {
-            const int sl = p0 + 2 * q + h;
-            u[h][0] = P.ux[sl]; u[h][1] = P.uy[sl]; u[h][2] = P.uz[sl];
-            w[h] = P.w[sl];
-            xp[h] = has_x ? P.x[sl] : 0.f;
-        }
-        uint32_t jfirst[2] = {0, 0};
-        if (pr.caseA)
-            for (int h = 0; h < nh; ++h) jfirst[h] = pr.pair_of_slot(2 * q + h);
-        for (uint32_t m = 0;; ++m) {
-            bool any = false;
-            const Philox4 ac = draw(q, cell, a.step, stream_tag(group, kAccept, m), a.seed);
-            for (int h = 0; h < nh; ++h) {
-                const uint32_t s = 2 * q + h;
-                uint32_t j, tau;
-                if (pr.caseA) {
-                    if (m > 0) continue;
-                    j = jfirst[h];
-                    tau = j % Nt;
-                } else {
-                    j = s + m * Np;
-                    if (j >= Nt) continue;
-                    tau = pr.target_of_pair(j);
+            const uint32_t s = 2 * q + h;
+            const int sl = p0 + (int)s;
+            float u[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
+            const float w = P.w[sl];
+            const float xp = has_x ? P.x[sl] : 0.f;
+            bool dirty = false;
+            if (pr.caseA) {
+                const uint32_t j = pr.pair_of_slot(s);
+                const Real UB = u01<Real>(ac.v[2 * h]), UT = u01<Real>(ac.v[2 * h + 1]);
+                if (!quick || UB < bB || UT < bT) {
+                    if (quick) acc.candidates[group]++;
+                    ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, w, xp, t0 + (int)(j % Nt), j, UB, UT, acc,
+                                  rad, wcre, dirty);
                 }
-                any = true;
-                const float before[3] = {u[h][0], u[h][1], u[h][2]};
-                ei_pair<Real>(a, tb, group, cell, mat, Zf, coef, u[h], w[h], xp[h], I, t0 + (int)tau, j,
-                              u01<Real>(ac.v[2 * h]), u01<Real>(ac.v[2 * h + 1]), acc, rad, wcre, had);
-                dirty[h] |= (before[0] != u[h][0]) | (before[1] != u[h][1]) | (before[2] != u[h][2]);
+            } else {
+                for (uint32_t m = 0, j = s; j < Nt; ++m, j += Np) {
+                    const Philox4 am = draw(q, cell, a.step, stream_tag(group, kAccept, m), a.seed);
+                    const Real UB = u01<Real>(am.v[2 * h]), UT = u01<Real>(am.v[2 * h + 1]);
+                    if (quick && !(UB < bB || UT < bT)) continue;
+                    acc.candidates[group]++;
+                    ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, w, xp, t0 + (int)pr.target_of_pair(j), j,
+                                  UB, UT, acc, rad, wcre, dirty);
+                }
             }
-            if (!any || pr.caseA) break;
+            if (dirty) {
+                P.ux[sl] = u[0]; P.uy[sl] = u[1]; P.uz[sl] = u[2];
+                had = true;
+            }
         }
-        for (int h = 0; h < nh; ++h)
-            if (dirty[h]) {
-                const int sl = p0 + 2 * q + h;
-                P.ux[sl] = u[h][0]; P.uy[sl] = u[h][1]; P.uz[sl] = u[h][2];
-            }
     }
     if (a.ledger && grp.any(had)) {
-        const float r = grp.sum(rad.s + (-rad.c)), wc = grp.sum(wcre.s + (-wcre.c));
+        const float r = grp.sum(rad), wc = grp.sum(wcre);
         if (grp.rank() == 0) {
             float4* L = reinterpret_cast<float4*>(a.ledger) + cell;
             float4 v = *L;
@@ -450,8 +600,9 @@ __device__ void ei_cell(const G& grp, const StepArgs& a, const Tab<Real>& tb, in
 
 // ---- one cell of photon - ion pairs (Bethe-Heitler) ---------------------------
 template <typename Real, class G>
-__device__ void bh_cell(const G& grp, const StepArgs& a, const Tab<Real>& tb, int cell, Acc& acc)
+__device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, int cell, Acc& acc)
 {
+    const StepArgs& a = *ap;
     const SpeciesView& P = a.ph;
     const SpeciesView& I = a.ion;
     const uint32_t Np = P.count[cell], Nt = I.count[cell];
@@ -462,105 +613,84 @@ __device__ void bh_cell(const G& grp, const StepArgs& a, const Tab<Real>& tb, in
         acc.status |= PCC_ST_NONFINITE;
         return;
     }
-    Real sp = 0, st = 0;
-    for (int s = grp.rank(); s < (int)Np; s += grp.size()) sp += (Real)P.w[p0 + s];
-    for (int s = grp.rank(); s < (int)Nt; s += grp.size()) st += (Real)I.w[t0 + s];
-    const Real n_p = grp.sum(sp), n_t = grp.sum(st);
     const Pairing pr = make_pairing(grp, Np, Nt, cell, kGroupPh, a);
-    Real spt = 0;
-    for (int s = grp.rank(); s < (int)Np; s += grp.size()) {
-        const float wp = P.w[p0 + s];
-        if (pr.caseA) {
-            spt += (Real)fminf(wp, I.w[t0 + pr.pair_of_slot(s) % Nt]);
-        } else {
-            for (uint32_t j = s; j < Nt; j += Np) spt += (Real)fminf(wp, I.w[t0 + pr.target_of_pair(j)]);
-        }
-    }
-    const Real n_pt = grp.sum(spt);
+    Real n_p, n_t, n_pt;
+    cell_sums<Real>(grp, P, I, p0, t0, Np, Nt, pr, n_p, n_t, n_pt);
     const Real coef = (n_p / n_pt) * n_t * (Real)(kC * a.dt);
     const uint32_t Npair = Np > Nt ? Np : Nt;
     if (grp.rank() == 0) acc.pairs[kGroupPh] += Npair;
     if (Npair > 65536u || (uint32_t)cell > 0xFFFFFFu || a.step > 0x7FFFFull) acc.status |= PCC_ST_ID_RANGE;
-    Kahan wcre;
+    float wcre = 0.f;
     bool absorbed_any = false;
     const bool has_x = P.x != nullptr;
+    const bool quick = sizeof(Real) == 4;
+    const Real bBH = quick ? coef * (Real)a.f_bound[3 * mat + 2] : (Real)0;
     for (uint32_t q = grp.rank(); 2 * q < Np; q += grp.size()) {
         const int nh = (2 * q + 1 < Np) ? 2 : 1;
-        bool dead[2] = {false, false};
-        uint32_t jfirst[2] = {0, 0};
-        if (pr.caseA)
-            for (int h = 0; h < nh; ++h) jfirst[h] = pr.pair_of_slot(2 * q + h);
-        for (uint32_t m = 0;; ++m) {
-            bool any = false;
-            const Philox4 ac = draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed);
-            for (int h = 0; h < nh; ++h) {
-                const uint32_t s = 2 * q + h;
+        Philox4 ac{};
+        if (pr.caseA) ac = draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, 0), a.seed);
+        for (int h = 0; h < nh; ++h) {
+            const uint32_t s = 2 * q + h;
+            const int sl = p0 + (int)s;
+            const uint32_t npass = pr.caseA ? 1u : (Nt - s + Np - 1) / Np;
+            bool loaded = false;
+            Real uk[3] = {0, 0, 0}, k = 0;
+            for (uint32_t m = 0; m < npass; ++m) {
                 uint32_t j, tau;
+                Real U;
                 if (pr.caseA) {
-                    if (m > 0) continue;
-                    j = jfirst[h];
+                    U = u01<Real>(ac.v[2 * h]);
+                } else {
+                    U = u01<Real>(draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed).v[2 * h]);
+                }
+                if (quick && !(U < bBH)) continue;   // exact quick reject
+                if (pr.caseA) {
+                    j = pr.pair_of_slot(s);
                     tau = j % Nt;
                 } else {
                     j = s + m * Np;
-                    if (j >= Nt) continue;
                     tau = pr.target_of_pair(j);
                 }
-                any = true;
-                if (dead[h]) continue;
-                const int sl = p0 + (int)s, ts = t0 + (int)tau;
-                const Real uk[3] = {(Real)P.ux[sl], (Real)P.uy[sl], (Real)P.uz[sl]};
-                const float wp = P.w[sl], wt = I.w[ts];
+                if (quick) acc.candidates[kGroupPh]++;
+                if (!loaded) {
+                    uk[0] = (Real)P.ux[sl]; uk[1] = (Real)P.uy[sl]; uk[2] = (Real)P.uz[sl];
+                    k = sqrt(uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
+                    loaded = true;
+                }
+                if (!isfinite(k)) { acc.status |= PCC_ST_NONFINITE; break; }
+                const int ts = t0 + (int)tau;
                 Frame<Real> f;
                 f.ui[0] = I.ux[ts]; f.ui[1] = I.uy[ts]; f.ui[2] = I.uz[ts];
                 f.gi = sqrt((Real)1 + f.ui[0] * f.ui[0] + f.ui[1] * f.ui[1] + f.ui[2] * f.ui[2]);
-                const Real k = sqrt(uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
                 const Real d = f.ui[0] * uk[0] + f.ui[1] * uk[1] + f.ui[2] * uk[2];
                 const Real kp = f.gi * k - d;
-                const Real fac = d / (f.gi + (Real)1) - k;
-                const Real pv[3] = {uk[0] + fac * f.ui[0], uk[1] + fac * f.ui[1], uk[2] + fac * f.ui[2]};
-                const Real pm = sqrt(pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]);
-                if (!isfinite(k)) { acc.status |= PCC_ST_NONFINITE; continue; }
-                const Real* row_tab = tb.hsig + (size_t)mat * a.g.n_rows;
-                const Real sig = sigma_at<Real>(tb, row_tab, a.g, kp - (Real)2, acc.status);
+                const Real sig = sigma_at<Real>(tb, tb.hsig + (size_t)mat * a.g.n_rows, a.g, kp - (Real)2, acc.status);
                 if (!(sig > (Real)0)) continue;
                 const Real x = coef * sig * kp / (k * f.gi);
                 if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
-                const Real U = u01<Real>(ac.v[2 * h]);
                 if (!(U < x && U < -expm1(-x))) continue;
                 acc.accepted[kChBH]++;
-                const Philox4 ev = draw(j, cell, a.step, stream_tag(kGroupPh, kEvtBH, 0), a.seed);
-                if ((wt < wp) && !(u01<Real>(ev.v[0]) < (Real)wt / (Real)wp)) continue;
-                acc.created[kChBH]++;
-                const Real* cdf = tb.hcdf + (size_t)mat * a.g.n_rows * a.g.n_cols;
-                const Real y = sample_col<Real>(cdf, a.g, kp - (Real)2, u01<Real>(ev.v[1]), u01<Real>(ev.v[2]), false,
-                                                0.0);
+                const Real fac = d / (f.gi + (Real)1) - k;
+                const Real pv[3] = {uk[0] + fac * f.ui[0], uk[1] + fac * f.ui[1], uk[2] + fac * f.ui[2]};
+                const Real pm = sqrt(pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]);
                 f.n[0] = pv[0] / pm; f.n[1] = pv[1] / pm; f.n[2] = pv[2] / pm;
-                Real up[3], um[3];
-                const Real Ep = lepton_to_lab(f, y * (kp - (Real)2), up);
-                const Real Em = lepton_to_lab(f, (kp - (Real)2) * ((Real)1 - y), um);
-                const float fm[3] = {(float)um[0], (float)um[1], (float)um[2]};
-                const float fp[3] = {(float)up[0], (float)up[1], (float)up[2]};
                 const float xpos = has_x ? P.x[sl] : 0.f;
-                const bool ok1 = append_particle(a.em, cell, fm, wp, xpos, has_x,
-                                                 secondary_pid(a.step, kChBH, cell, j, 0), acc.status);
-                const bool ok2 = append_particle(a.ep, cell, fp, wp, xpos, has_x,
-                                                 secondary_pid(a.step, kChBH, cell, j, 1), acc.status);
-                if (ok1 && ok2) {
-                    acc.dE += (double)wp * ((double)Ep + (double)Em - (double)k);
-                    wcre.add(2.f * wp);
-                }
-                dead[h] = true;
-                P.w[sl] = 0.f;   // removal marker, compacted below
+                const EventResult r = bh_event<Real>(ap, tb, cell, mat, j, P.w[sl], I.w[ts], xpos, f, kp, k);
+                if (!r.created) continue;
+                acc.created[kChBH]++;
+                acc.dE += r.dE;
+                acc.status |= r.status;
+                wcre += r.wc;
+                P.w[sl] = 0.f;   // removal marker, compacted below; skips the photon's later pairs
                 absorbed_any = true;
+                break;
             }
-            if (!any || pr.caseA) break;
         }
     }
-    const bool anyd = grp.any(absorbed_any);
-    if (anyd) {
+    if (grp.any(absorbed_any)) {
         grp.sync();
         if (a.ledger) {
-            const float wc = grp.sum(wcre.s + (-wcre.c));
+            const float wc = grp.sum(wcre);
             if (grp.rank() == 0) {
                 float4* L = reinterpret_cast<float4*>(a.ledger) + cell;
                 float4 v = *L;
@@ -593,21 +723,23 @@ __device__ void bh_cell(const G& grp, const StepArgs& a, const Tab<Real>& tb, in
 __device__ void flush_acc(Acc& acc, DevStats* st, bool lane_reduce)
 {
     unsigned long long pv[3];
-    unsigned av[5], cv[5];
+    unsigned av[5], cv[5], kv[3];
     double dE = acc.dE, dQ = acc.dQ;
     unsigned status = acc.status;
-    for (int i = 0; i < 3; ++i) pv[i] = acc.pairs[i];
+    for (int i = 0; i < 3; ++i) pv[i] = acc.pairs[i], kv[i] = acc.candidates[i];
     for (int i = 0; i < 5; ++i) { av[i] = acc.accepted[i]; cv[i] = acc.created[i]; }
     if (lane_reduce) {
-        for (int i = 0; i < 3; ++i) pv[i] = warp_sum(pv[i]);
+        for (int i = 0; i < 3; ++i) pv[i] = warp_sum(pv[i]), kv[i] = warp_sum(kv[i]);
         for (int i = 0; i < 5; ++i) { av[i] = warp_sum(av[i]); cv[i] = warp_sum(cv[i]); }
         dE = warp_sum(dE);
         dQ = warp_sum(dQ);
         status = __reduce_or_sync(0xffffffffu, status);
         if ((threadIdx.x & 31) != 0) return;
     }
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i) {
         if (pv[i]) atomicAdd(&st->pairs[i], pv[i]);
+        if (kv[i]) atomicAdd(&st->candidates[i], (unsigned long long)kv[i]);
+    }
     for (int i = 0; i < 5; ++i) {
         if (av[i]) atomicAdd(&st->accepted[i], (unsigned long long)av[i]);
         if (cv[i]) atomicAdd(&st->created[i], (unsigned long long)cv[i]);
@@ -619,7 +751,7 @@ __device__ void flush_acc(Acc& acc, DevStats* st, bool lane_reduce)
 
 // Plain FP64: one block per cell.
 template <int GROUP>
-__global__ void __launch_bounds__(128) collide_plain_kernel(StepArgs a)
+__global__ void __launch_bounds__(128) collide_plain_kernel(const __grid_constant__ StepArgs a)
 {
     __shared__ int scratch[64];
     __shared__ double red[4];
@@ -628,65 +760,657 @@ __global__ void __launch_bounds__(128) collide_plain_kernel(StepArgs a)
     Acc acc;
     acc.zero();
     const int cell = blockIdx.x;
-    if (GROUP == kGroupPh) bh_cell<double>(grp, a, tb, cell, acc);
-    else ei_cell<double>(grp, a, tb, GROUP, cell, acc);
+    if (GROUP == kGroupPh) bh_cell<double>(grp, &a, tb, cell, acc);
+    else ei_cell<double>(grp, &a, tb, GROUP, cell, acc);
     flush_acc(acc, a.st, true);
 }
 
-// Batched FP32: persistent grid, one warp per cell.
+// Batched FP32 -----------------------------------------------------------------
+// Every cell with both lists non-empty is processed by one warp.  Cells are
+// listed by decreasing size class (bit length of N_pair) and dealt to the
+// warps of a persistent grid round-robin, so each warp receives a similar
+// share of large and small cells.
 constexpr int kBatchedThreads = 256;
+constexpr int kClasses = 18;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+struct CellList {
+    int* list;       // [n_cells], cells by decreasing size class
+    int* hist;       // [kClasses]
+    int* cursor;     // [kClasses]
+};
+
+__device__ __forceinline__ int size_class(int np, int nt)
+{
+    const int n = np > nt ? np : nt;
+    const int b = 32 - __clz(n);
+    return b < kClasses ? b : kClasses - 1;
+}
+
+__global__ void class_hist_kernel(const int* __restrict__ cnt_p, const int* __restrict__ cnt_t, int n_cells,
+                                  CellList L)
+{
+    __shared__ int h[kClasses];
+    if (threadIdx.x < kClasses) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n_cells) {
+        const int np = cnt_p[c], nt = cnt_t[c];
+        if (np > 0 && nt > 0) atomicAdd(&h[size_class(np, nt)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses && h[threadIdx.x]) atomicAdd(&L.hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void class_scatter_kernel(const int* __restrict__ cnt_p, const int* __restrict__ cnt_t, int n_cells,
+                                     CellList L)
+{
+    __shared__ int off[kClasses];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int k = kClasses - 1; k >= 0; --k) {
+            off[k] = acc;
+            acc += L.hist[k];
+        }
+    }
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int cls = -1;
+    if (c < n_cells) {
+        const int np = cnt_p[c], nt = cnt_t[c];
+        if (np > 0 && nt > 0) cls = size_class(np, nt);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, cls);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (cls >= 0 && lane == leader) base = atomicAdd(&L.cursor[cls], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    if (cls >= 0) L.list[off[cls] + base + __popc(peers & ((1u << lane) - 1u))] = c;
+}
+
+// Stage the ln sigma rows (n_mat x n_rows floats) in shared memory with one
+// bulk copy; returns the shared copy, or the global one if the wait gives up.
+__device__ const float* stage_table(const float* src, int bytes, unsigned char* dyn, unsigned long long* bar,
+                                    unsigned& status)
+{
+    if (bytes <= 0) return src;
+    const uint32_t b = smem_u32(bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(dyn)),
+                     "l"(src), "r"(bytes), "r"(b)
+                     : "memory");
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(b)
+            : "memory");
+    }
+    const int all = __syncthreads_and((int)done);
+    if (!all) {
+        status |= PCC_ST_TIMEOUT;
+        return src;
+    }
+    return reinterpret_cast<const float*>(dyn);
+}
+
 template <int GROUP>
-__global__ void __launch_bounds__(kBatchedThreads) collide_batched_kernel(StepArgs a, int stage_bytes)
+__device__ __forceinline__ Tab<float> batched_tab(const StepArgs& a, const float* staged)
+{
+    return Tab<float>{GROUP == kGroupPh ? a.f_brems_lnsig : staged, a.f_brems_cdf,
+                      GROUP == kGroupPh ? staged : a.f_bh_lnsig, a.f_bh_cdf, a.f_tri_gp, a.f_tri_split};
+}
+
+// j mod n for j < 2^24 via a float reciprocal (exact after the correction).
+__device__ __forceinline__ uint32_t fast_mod(uint32_t j, uint32_t n, float inv_n)
+{
+    uint32_t q = __float2uint_rz((float)j * inv_n);
+    int r = (int)j - (int)(q * n);
+    if (r < 0) r += (int)n;
+    if (r >= (int)n) r -= (int)n;
+    return (uint32_t)r;
+}
+
+// Per-cell metadata, loaded one cell ahead by the persistent loop.
+struct CellMeta {
+    int cell, p0, t0, mat;
+    uint32_t Np, Nt;
+};
+
+__device__ __forceinline__ CellMeta load_meta(const StepArgs& a, const SpeciesView& P, int cell)
+{
+    CellMeta m;
+    m.cell = cell;
+    // a list entry outside [0, n_cells) is skipped (never read through)
+    if (cell < 0 || cell >= a.n_cells) { m.Np = m.Nt = 0; m.p0 = m.t0 = m.mat = 0; return m; }
+    m.Np = P.count[cell];
+    m.Nt = a.ion.count[cell];
+    m.p0 = P.start[cell];
+    m.t0 = a.ion.start[cell];
+    m.mat = a.mat_of_cell[cell];
+    return m;
+}
+
+// Per-block counters of the batched kernels, updated with shared atomics and
+// added to the context's counters once per block.
+struct BlockAcc {
+    unsigned long long pairs[3], accepted[5], created[5], candidates[3];
+    double dE;
+    unsigned status;
+};
+
+__device__ __forceinline__ void block_acc_init(BlockAcc& b)
+{
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 3; ++i) b.pairs[i] = b.candidates[i] = 0;
+        for (int i = 0; i < 5; ++i) b.accepted[i] = b.created[i] = 0;
+        b.dE = 0.0;
+        b.status = 0;
+    }
+}
+
+__device__ __forceinline__ void block_acc_flush(const BlockAcc& b, DevStats* st)
+{
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i < 3; ++i) {
+        if (b.pairs[i]) atomicAdd(&st->pairs[i], b.pairs[i]);
+        if (b.candidates[i]) atomicAdd(&st->candidates[i], b.candidates[i]);
+    }
+    for (int i = 0; i < 5; ++i) {
+        if (b.accepted[i]) atomicAdd(&st->accepted[i], b.accepted[i]);
+        if (b.created[i]) atomicAdd(&st->created[i], b.created[i]);
+    }
+    if (b.dE != 0.0) atomicAdd(&st->energy_change, b.dE);
+    if (b.status) atomicOr(&st->status, b.status);
+}
+
+// Candidate queues and per-call cell state of the batched path.
+struct Queue {
+    uint2* flat;          // [cap_flat] (cell, projectile slot) of candidates in cells with N_p >= N_t
+    int* flat_count;      // [1]
+    uint32_t cap_flat;
+    uint32_t* qb;         // [target capacity] pair indices of candidates in cells with N_p < N_t,
+                          // written into the cell's target region in increasing pair order per projectile
+    int* cand;            // [n_cells] such candidates of the cell
+    float* coef;          // [n_cells] (n_p n_t / n_pt) c dt
+    int* caseb;           // [n_cells] cells with N_p < N_t and candidates
+    int* caseb_count;     // [1]
+    int* flagged;         // [n_cells] cells with an event in this call
+    int* flagged_count;   // [1]
+    int* flag;            // [n_cells] 1 once listed (cleared by the finalize kernel)
+    float2* evacc;        // [n_cells] this call's ledger contributions (radiated energy, created weight)
+};
+
+__device__ __forceinline__ void flag_cell(const Queue& Q, int cell)
+{
+    if (atomicCAS(&Q.flag[cell], 0, 1) == 0) Q.flagged[atomicAdd(Q.flagged_count, 1)] = cell;
+}
+
+// Acceptance bounds of the group at this coefficient, as integer thresholds
+// on the 23 uniform bits: U = ((r >> 9) + 1/2) 2^-23 < b  <=>  (r >> 9) < ceil(b 2^23 - 1/2).
+template <int GROUP>
+__device__ __forceinline__ void bound_thresholds(const StepArgs& a, int mat, float coef, uint32_t& k1, uint32_t& k2)
+{
+    float b1, b2;
+    if (GROUP == kGroupPh) {
+        b1 = coef * a.f_bound[3 * mat + 2];
+        b2 = 0.f;
+    } else {
+        b1 = (a.mask & PCC_BREMS) ? coef * a.f_bound[3 * mat] : 0.f;
+        b2 = (a.mask & PCC_TRIDENT) ? coef * a.f_bound[3 * mat + 1] : 0.f;
+    }
+    k1 = (uint32_t)fminf(ceilf(b1 * 8388608.0f - 0.5f), 8388608.0f);
+    k2 = (uint32_t)fminf(ceilf(b2 * 8388608.0f - 0.5f), 8388608.0f);
+}
+
+// One photon-ion candidate pair (Bethe-Heitler); returns true when the photon
+// is absorbed (its weight is then set to 0 for the compaction).
+__device__ __forceinline__ bool bh_candidate(const StepArgs& a, const Tab<float>& tb, int cell, int mat, float coef,
+                                             int sl, int ts, uint32_t j, float U, Acc& acc, float& wcre)
+{
+    const SpeciesView& P = a.ph;
+    const SpeciesView& I = a.ion;
+    const float uk[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
+    const float k = sqrtf(uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
+    if (!isfinite(k)) {
+        acc.status |= PCC_ST_NONFINITE;
+        return false;
+    }
+    Frame<float> f;
+    f.ui[0] = I.ux[ts]; f.ui[1] = I.uy[ts]; f.ui[2] = I.uz[ts];
+    f.gi = q_sqrt1(1.f + f.ui[0] * f.ui[0] + f.ui[1] * f.ui[1] + f.ui[2] * f.ui[2]);
+    const float d = f.ui[0] * uk[0] + f.ui[1] * uk[1] + f.ui[2] * uk[2];
+    const float kp = f.gi * k - d;
+    const float sig = sigma_at<float>(tb, tb.hsig + (size_t)mat * a.g.n_rows, a.g, kp - 2.f, acc.status);
+    if (!(sig > 0.f)) return false;
+    const float x = q_div(coef * sig * kp, k * f.gi);
+    if (x > 1.f) acc.status |= PCC_ST_PROB_LARGE;
+    if (!(U < x && U < -expm1f(-x))) return false;
+    acc.accepted[kChBH]++;
+    const float fac = q_div(d, f.gi + 1.f) - k;
+    const float pv[3] = {uk[0] + fac * f.ui[0], uk[1] + fac * f.ui[1], uk[2] + fac * f.ui[2]};
+    const float pm = sqrtf(pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]);
+    f.n[0] = pv[0] / pm; f.n[1] = pv[1] / pm; f.n[2] = pv[2] / pm;
+    const float xpos = P.x ? P.x[sl] : 0.f;
+    const EventResult r = bh_event<float>(&a, tb, cell, mat, j, P.w[sl], I.w[ts], xpos, f, kp, k);
+    if (!r.created) return false;
+    acc.created[kChBH]++;
+    acc.dE += r.dE;
+    acc.status |= r.status;
+    wcre += r.wc;
+    P.w[sl] = 0.f;   // removal marker
+    return true;
+}
+
+constexpr int kWarpBuf = 128;   // per-warp staging of candidates before the flat queue
+
+// Scan: for each cell (one warp), the sums n_p, n_t, n_pt of Sec. III.A, the
+// coefficient, and the accept uniforms of every pair against the
+// per-material bounds.  Pairs at or above the bounds are rejected here,
+// exactly (U >= bound >= x >= 1 - exp(-x)), without reading the particle
+// records; the others are queued.  Lane l owns slots base + 2l and
+// base + 2l + 1, whose uniforms are the four words of its own Philox draw.
+// Contains no calls, so its loop state stays in registers.
+template <int GROUP, int MINB>
+__global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __grid_constant__ StepArgs a, CellList L,
+                                                                     Queue Q)
+{
+    __shared__ int scratch[kBatchedThreads / 32][64];
+    __shared__ uint2 buf[kBatchedThreads / 32][kWarpBuf];
+    __shared__ BlockAcc bacc;
+    block_acc_init(bacc);
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* tab = scratch[wid];
+    uint2* wb = buf[wid];
+    int nb = 0;   // staged candidates of this warp (warp-uniform)
+    int n = 0;
+    for (int k = 0; k < kClasses; ++k) n += L.hist[k];
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const SpeciesView& P = GROUP == kGroupEm ? a.em : (GROUP == kGroupEp ? a.ep : a.ph);
+    const SpeciesView& I = a.ion;
+    const uint32_t step32 = (uint32_t)a.step;
+    int kk = blockIdx.x * (blockDim.x >> 5) + wid;
+    CellMeta next = load_meta(a, P, kk < n ? L.list[kk] : -1);
+    while (kk < n) {
+        const CellMeta cm = next;
+        kk += nwarps;
+        next = load_meta(a, P, kk < n ? L.list[kk] : -1);   // prefetch
+        const uint32_t Np = cm.Np, Nt = cm.Nt;
+        const int cell = cm.cell, p0 = cm.p0, t0 = cm.t0, mat = cm.mat;
+        if (Np == 0 || Nt == 0) continue;
+        if ((unsigned)mat >= (unsigned)a.n_mat) {
+            if (lane == 0) atomicOr(&bacc.status, PCC_ST_NONFINITE);
+            continue;
+        }
+        const bool caseA = Np >= Nt;
+        // ---- sums
+        const float w0 = I.w[t0];
+        float sp = 0.f, st = 0.f, sf = 0.f;
+        bool uni = true;
+#pragma unroll 4
+        for (uint32_t s = lane; s < Nt; s += 32) {
+            const float wt = I.w[t0 + s];
+            st += wt;
+            uni &= (wt == w0);
+        }
+        if (caseA) {
+#pragma unroll 4
+            for (uint32_t s = lane; s < Np; s += 32) {
+                const float wp = P.w[p0 + s];
+                sp += wp;
+                sf += fminf(wp, w0);
+            }
+        } else {   // projectile s takes part in ceil((N_t - s) / N_p) pairs
+            for (uint32_t s = lane; s < Np; s += 32) {
+                const float wp = P.w[p0 + s];
+                sp += wp;
+                sf += fminf(wp, w0) * (float)((Nt - s + Np - 1) / Np);
+            }
+        }
+        const float n_p = warp_sum(sp), n_t = warp_sum(st);
+        float n_pt;
+        if (__all_sync(0xffffffffu, uni)) {
+            n_pt = warp_sum(sf);
+        } else {   // unequal target weights: sum over the actual pairs
+            const Philox4 kp = draw_k(0, (uint32_t)cell, step32, stream_tag(GROUP, kPerm, 0), a.keys);
+            PermKeys rk;
+            rk.k[0] = kp.v[0]; rk.k[1] = kp.v[1]; rk.k[2] = kp.v[2]; rk.k[3] = kp.v[3];
+            const uint32_t NL = caseA ? Np : Nt;
+            if (NL <= 32) {
+                __syncwarp();
+                if (lane < (int)NL) {
+                    const uint32_t r = perm_pos_small(lane, NL, rk);
+                    tab[r] = lane;    // P table
+                    tab[32 + lane] = r;
+                }
+                __syncwarp();
+            }
+            float spt = 0.f;
+            const float inv_nt = 1.0f / (float)Nt;
+            for (uint32_t s = lane; s < Np; s += 32) {
+                const float wp = P.w[p0 + s];
+                if (caseA) {
+                    const uint32_t j = NL <= 32 ? (uint32_t)tab[32 + s] : perm_pos_large(s, Np, rk);
+                    spt += fminf(wp, I.w[t0 + fast_mod(j, Nt, inv_nt)]);
+                } else {
+                    for (uint32_t j = s; j < Nt; j += Np) {
+                        const uint32_t t = NL <= 32 ? (uint32_t)tab[j] : perm_elem_large(j, Nt, rk);
+                        spt += fminf(wp, I.w[t0 + t]);
+                    }
+                }
+            }
+            n_pt = warp_sum(spt);
+        }
+        const float coef = __fdividef(n_p, n_pt) * n_t * a.f_cdt;
+        uint32_t k1, k2;
+        bound_thresholds<GROUP>(a, mat, coef, k1, k2);
+        const uint32_t tag0 = stream_tag(GROUP, kAccept, 0);
+        uint32_t ncand = 0;
+        if (caseA) {
+            for (uint32_t base = 0; base < Np; base += 64) {
+                const Philox4 ph = draw_k((base >> 1) + lane, (uint32_t)cell, step32, tag0, a.keys);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t s = base + 2 * lane + h;
+                    const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
+                    const bool cand = s < Np && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
+                    const unsigned m = __ballot_sync(0xffffffffu, cand);
+                    if (cand) wb[nb + __popc(m & ((1u << lane) - 1u))] = make_uint2((uint32_t)cell, s);
+                    nb += __popc(m);
+                    ncand += __popc(m);
+                }
+                if (nb > kWarpBuf - 64) {   // flush the staging buffer to the flat queue
+                    __syncwarp();
+                    int base_q = 0;
+                    if (lane == 0) base_q = atomicAdd(Q.flat_count, nb);
+                    base_q = __shfl_sync(0xffffffffu, base_q, 0);
+                    for (int i = lane; i < nb; i += 32)
+                        if ((uint32_t)(base_q + i) < Q.cap_flat) Q.flat[base_q + i] = wb[i];
+                    if (lane == 0 && (uint32_t)(base_q + nb) > Q.cap_flat) atomicOr(&bacc.status, PCC_ST_CAPACITY);
+                    nb = 0;
+                    __syncwarp();
+                }
+            }
+        } else {
+            uint32_t cnt = 0;
+            for (uint32_t q0 = 0; 2 * q0 < Np; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                const uint32_t passes = (Nt + Np - 1) / Np;
+                for (uint32_t mp = 0; mp < passes; ++mp) {
+                    const Philox4 ph = draw_k(q, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t s = 2 * q + h, j = s + mp * Np;
+                        const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
+                        const bool cand = s < Np && j < Nt && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
+                        const unsigned m = __ballot_sync(0xffffffffu, cand);
+                        if (cand) Q.qb[t0 + cnt + __popc(m & ((1u << lane) - 1u))] = j;
+                        cnt += __popc(m);
+                    }
+                }
+            }
+            if (lane == 0) {
+                Q.cand[cell] = (int)cnt;
+                if (cnt) Q.caseb[atomicAdd(Q.caseb_count, 1)] = cell;
+            }
+            ncand = cnt;
+        }
+        if (lane == 0) {
+            Q.coef[cell] = coef;
+            atomicAdd(&bacc.pairs[GROUP], (unsigned long long)(caseA ? Np : Nt));
+            if (ncand) atomicAdd(&bacc.candidates[GROUP], (unsigned long long)ncand);
+            if ((caseA ? Np : Nt) > 65536u || (uint32_t)cell > 0xFFFFFFu || a.step > 0x7FFFFull)
+                atomicOr(&bacc.status, PCC_ST_ID_RANGE);
+        }
+    }
+    if (nb > 0) {   // final flush
+        __syncwarp();
+        int base_q = 0;
+        if (lane == 0) base_q = atomicAdd(Q.flat_count, nb);
+        base_q = __shfl_sync(0xffffffffu, base_q, 0);
+        for (int i = lane; i < nb; i += 32)
+            if ((uint32_t)(base_q + i) < Q.cap_flat) Q.flat[base_q + i] = wb[i];
+        if (lane == 0 && (uint32_t)(base_q + nb) > Q.cap_flat) atomicOr(&bacc.status, PCC_ST_CAPACITY);
+    }
+    __syncthreads();
+    block_acc_flush(bacc, a.st);
+}
+
+// Fold the per-thread counters of a batched kernel into the block, then the context.
+__device__ __forceinline__ void fold_acc(Acc& acc, BlockAcc& bacc, DevStats* st)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = 0; i < 5; ++i) {
+        const unsigned av = warp_sum(acc.accepted[i]), cv = warp_sum(acc.created[i]);
+        if (lane == 0) {
+            if (av) atomicAdd(&bacc.accepted[i], (unsigned long long)av);
+            if (cv) atomicAdd(&bacc.created[i], (unsigned long long)cv);
+        }
+    }
+    const double dE = warp_sum(acc.dE);
+    const unsigned stt = __reduce_or_sync(0xffffffffu, acc.status);
+    if (lane == 0) {
+        if (dE != 0.0) atomicAdd(&bacc.dE, dE);
+        if (stt) atomicOr(&bacc.status, stt);
+    }
+    __syncthreads();
+    block_acc_flush(bacc, st);
+}
+
+// Candidates of cells with N_p >= N_t (one pair per projectile), one thread
+// each: pairing, ion frame, cross section, acceptance, events.  Event
+// contributions to the cell ledger are gathered per cell (float atomics) and
+// the cell is listed for the finalize kernel.
+template <int GROUP>
+__global__ void __launch_bounds__(kBatchedThreads, 4) flat_cand_kernel(const __grid_constant__ StepArgs a, Queue Q,
+                                                                       int stage_bytes)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ BlockAcc bacc;
+    __shared__ __align__(8) unsigned long long bar;
+    block_acc_init(bacc);
+    unsigned st0 = 0;
+    const float* ls = stage_table(GROUP == kGroupPh ? a.f_bh_lnsig : a.f_brems_lnsig, stage_bytes, dyn, &bar, st0);
+    if (st0 && threadIdx.x == 0) bacc.status |= st0;
+    __syncthreads();
+    const Tab<float> tb = batched_tab<GROUP>(a, ls);
+    const SpeciesView& P = GROUP == kGroupEm ? a.em : (GROUP == kGroupEp ? a.ep : a.ph);
+    const uint32_t step32 = (uint32_t)a.step;
+    const int total = min(*Q.flat_count, (int)Q.cap_flat);
+    Acc acc;
+    acc.zero();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const uint2 e = Q.flat[i];
+        const int cell = (int)e.x;
+        const uint32_t s = e.y;
+        if (cell < 0 || cell >= a.n_cells) continue;
+        const CellMeta cm = load_meta(a, P, cell);
+        const uint32_t Np = cm.Np, Nt = cm.Nt;
+        const float coef = Q.coef[cell];
+        const Philox4 kp = draw_k(0, (uint32_t)cell, step32, stream_tag(GROUP, kPerm, 0), a.keys);
+        PermKeys rk;
+        rk.k[0] = kp.v[0]; rk.k[1] = kp.v[1]; rk.k[2] = kp.v[2]; rk.k[3] = kp.v[3];
+        const uint32_t j = Np <= 32 ? perm_pos_small(s, Np, rk) : perm_pos_large(s, Np, rk);
+        const int ts = cm.t0 + (int)fast_mod(j, Nt, 1.0f / (float)Nt);
+        const Philox4 ph = draw_k(s >> 1, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, 0), a.keys);
+        const uint32_t r1 = ph.v[2 * (s & 1u)], r2 = ph.v[2 * (s & 1u) + 1];
+        const int sl = cm.p0 + (int)s;
+        float rad = 0.f, wcre = 0.f;
+        bool event = false;
+        if (GROUP == kGroupPh) {
+            event = bh_candidate(a, tb, cell, cm.mat, coef, sl, ts, j, u01<float>(r1), acc, wcre);
+        } else {
+            float u[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
+            const float xp = P.x ? P.x[sl] : 0.f;
+            ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w[sl], xp, ts, j, u01<float>(r1),
+                           u01<float>(r2), acc, rad, wcre, event);
+            if (event) {
+                P.ux[sl] = u[0]; P.uy[sl] = u[1]; P.uz[sl] = u[2];
+            }
+        }
+        if (event) {
+            if (rad != 0.f) atomicAdd(&Q.evacc[cell].x, rad);
+            if (wcre != 0.f) atomicAdd(&Q.evacc[cell].y, wcre);
+            flag_cell(Q, cell);
+        }
+    }
+    fold_acc(acc, bacc, a.st);
+}
+
+// Candidates of cells with N_p < N_t, one warp per cell, in queue order on
+// one lane (a projectile's pairs in increasing pair index; a photon absorbed
+// on an earlier pair skips its later ones).
+template <int GROUP>
+__global__ void __launch_bounds__(kBatchedThreads, 2) caseb_cand_kernel(const __grid_constant__ StepArgs a, Queue Q,
+                                                                        int stage_bytes)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ int scratch[kBatchedThreads / 32][64];
+    __shared__ BlockAcc bacc;
     __shared__ __align__(8) unsigned long long bar;
-    const int wid = threadIdx.x >> 5;
-    WarpGroup grp{scratch[wid]};
-    const float* lnsig_src = GROUP == kGroupPh ? a.f_bh_lnsig : a.f_brems_lnsig;
-    const float* lnsig = lnsig_src;
+    block_acc_init(bacc);
+    unsigned st0 = 0;
+    const float* ls = stage_table(GROUP == kGroupPh ? a.f_bh_lnsig : a.f_brems_lnsig, stage_bytes, dyn, &bar, st0);
+    if (st0 && threadIdx.x == 0) bacc.status |= st0;
+    __syncthreads();
+    const Tab<float> tb = batched_tab<GROUP>(a, ls);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* tab = scratch[wid];
+    const int n = *Q.caseb_count;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const SpeciesView& P = GROUP == kGroupEm ? a.em : (GROUP == kGroupEp ? a.ep : a.ph);
+    const uint32_t step32 = (uint32_t)a.step;
     Acc acc;
     acc.zero();
-    if (stage_bytes > 0) {
-        // Bulk copy of the ln sigma rows of every material into shared memory.
-        const uint32_t b = smem_u32(&bar);
-        if (threadIdx.x == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int kk = blockIdx.x * (blockDim.x >> 5) + wid; kk < n; kk += nwarps) {
+        const int cell = Q.caseb[kk];
+        if (cell < 0 || cell >= a.n_cells) continue;
+        const CellMeta cm = load_meta(a, P, cell);
+        const uint32_t Np = cm.Np, Nt = cm.Nt;
+        const int cnt = Q.cand[cell];
+        const float coef = Q.coef[cell];
+        const Philox4 kp = draw_k(0, (uint32_t)cell, step32, stream_tag(GROUP, kPerm, 0), a.keys);
+        PermKeys rk;
+        rk.k[0] = kp.v[0]; rk.k[1] = kp.v[1]; rk.k[2] = kp.v[2]; rk.k[3] = kp.v[3];
+        if (Nt <= 32) {   // P table of the targets
+            __syncwarp();
+            if (lane < (int)Nt) tab[perm_pos_small(lane, Nt, rk)] = lane;
+            __syncwarp();
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(stage_bytes)
-                         : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(dyn)),
-                "l"(lnsig_src), "r"(stage_bytes), "r"(b)
-                : "memory");
+        if (lane == 0) {
+            float rad = 0.f, wcre = 0.f;
+            bool any = false;
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t j = Q.qb[cm.t0 + k];
+                const uint32_t s = j % Np, mp = j / Np;
+                const Philox4 ph = draw_k(s >> 1, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
+                const uint32_t r1 = ph.v[2 * (s & 1u)], r2 = ph.v[2 * (s & 1u) + 1];
+                const uint32_t t = Nt <= 32 ? (uint32_t)tab[j] : perm_elem_large(j, Nt, rk);
+                const int ts = cm.t0 + (int)t, sl = cm.p0 + (int)s;
+                bool event = false;
+                if (GROUP == kGroupPh) {
+                    if (P.w[sl] == 0.f) continue;   // absorbed earlier in this step
+                    event = bh_candidate(a, tb, cell, cm.mat, coef, sl, ts, j, u01<float>(r1), acc, wcre);
+                } else {
+                    float u[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
+                    const float xp = P.x ? P.x[sl] : 0.f;
+                    ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w[sl], xp, ts, j,
+                                   u01<float>(r1), u01<float>(r2), acc, rad, wcre, event);
+                    if (event) {
+                        P.ux[sl] = u[0]; P.uy[sl] = u[1]; P.uz[sl] = u[2];
+                    }
+                }
+                any |= event;
+            }
+            if (any) {
+                if (rad != 0.f) atomicAdd(&Q.evacc[cell].x, rad);
+                if (wcre != 0.f) atomicAdd(&Q.evacc[cell].y, wcre);
+                flag_cell(Q, cell);
+            }
         }
-        uint32_t done = 0;
-        for (int it = 0; it < (1 << 22) && !done; ++it) {
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-                : "=r"(done)
-                : "r"(b)
-                : "memory");
-        }
-        if (done) lnsig = reinterpret_cast<const float*>(dyn);
-        else acc.status |= PCC_ST_TIMEOUT;   // keep reading the global copy
-        __syncthreads();
+        __syncwarp();
     }
-    Tab<float> tb{GROUP == kGroupPh ? a.f_brems_lnsig : lnsig, a.f_brems_cdf, GROUP == kGroupPh ? lnsig : a.f_bh_lnsig,
-                  a.f_bh_cdf, a.f_tri_gp, a.f_tri_split};
+    fold_acc(acc, bacc, a.st);
+}
+
+// Stable removal of the absorbed photons (weight 0) from the first Np slots
+// of a cell region, keeping the order of the rest (including the Np..n_all
+// secondaries appended in this step), one warp: each 32-record chunk is read
+// into registers before any write, and destinations never pass sources.
+__device__ void compact_region_warp(const SpeciesView& P, int cell)
+{
+    const int lane = threadIdx.x & 31;
+    const int p0 = P.start[cell], Np = P.count[cell];
+    const int n_all = Np + P.added[cell];
+    const bool has_x = P.x != nullptr;
+    int wr = 0;   // warp-uniform write position
+    for (int c0 = 0; c0 < n_all; c0 += 32) {
+        const int i = c0 + lane;
+        const bool in = i < n_all;
+        float ux = 0.f, uy = 0.f, uz = 0.f, w = 0.f, x = 0.f;
+        uint64_t pid = 0;
+        if (in) {
+            const int src = p0 + i;
+            ux = P.ux[src]; uy = P.uy[src]; uz = P.uz[src]; w = P.w[src];
+            if (has_x) x = P.x[src];
+            pid = P.pid[src];
+        }
+        const bool keep = in && !(i < Np && w == 0.f);
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) {
+            const int dst = p0 + wr + __popc(m & ((1u << lane) - 1u));
+            if (dst != p0 + i) {
+                P.ux[dst] = ux; P.uy[dst] = uy; P.uz[dst] = uz; P.w[dst] = w;
+                if (has_x) P.x[dst] = x;
+                P.pid[dst] = pid;
+            }
+        }
+        wr += __popc(m);
+        __syncwarp();
+    }
+    if (lane == 0) P.count[cell] = wr - P.added[cell];
+}
+
+// Cells with an event in this call, one warp each: the Kahan update of the
+// cell ledger from the gathered contributions and (photons) the compaction
+// that removes absorbed photons.
+template <int GROUP>
+__global__ void finalize_kernel(const __grid_constant__ StepArgs a, Queue Q)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = *Q.flagged_count;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int cell = blockIdx.x * (blockDim.x >> 5) + wid; cell < a.n_cells; cell += nwarps) {
-        if (GROUP == kGroupPh) bh_cell<float>(grp, a, tb, cell, acc);
-        else ei_cell<float>(grp, a, tb, GROUP, cell, acc);
+    for (int kk = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); kk < n; kk += nwarps) {
+        const int cell = Q.flagged[kk];
+        if (cell < 0 || cell >= a.n_cells) continue;
+        if (lane == 0) {
+            const float2 ev = Q.evacc[cell];
+            if (a.ledger) {
+                float4* Lg = reinterpret_cast<float4*>(a.ledger) + cell;
+                float4 v = *Lg;
+                Kahan ka{v.x, v.y}, kb{v.z, v.w};
+                ka.add(ev.x);
+                kb.add(ev.y);
+                *Lg = make_float4(ka.s, ka.c, kb.s, kb.c);
+            }
+            Q.evacc[cell] = make_float2(0.f, 0.f);
+        }
+        if (GROUP == kGroupPh) compact_region_warp(a.ph, cell);
+        __syncwarp();
+        if (lane == 0) Q.flag[cell] = 0;
     }
-    flush_acc(acc, a.st, true);
 }
 
 // Pairing diagnostic: one warp per cell.
@@ -748,17 +1472,136 @@ static StepArgs make_args(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em,
     a.f_brems_lnsig = ctx->f_brems_lnsig; a.f_brems_cdf = ctx->f_brems_cdf;
     a.f_bh_lnsig = ctx->f_bh_lnsig; a.f_bh_cdf = ctx->f_bh_cdf;
     a.f_tri_gp = ctx->f_tri_gp_cdf; a.f_tri_split = ctx->f_tri_split_cdf; a.f_Z = ctx->f_Z;
+    a.f_bound = ctx->f_bound;
+    a.keys = philox_keys(seed);
+    a.f_cdt = (float)(kC * dt);
     a.st = ctx->stats;
     return a;
 }
 
-// Blocks of the persistent batched kernel: resident blocks per SM x SMs.
-static int batched_grid(pcc_ctx* ctx, const void* fn, int smem)
+// Blocks of a persistent kernel: resident blocks per SM (or the tuned count) x SMs.
+static int persistent_grid(pcc_ctx* ctx, const void* fn, int smem, int want_per_sm)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchedThreads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
+    if (want_per_sm > 0 && want_per_sm < per_sm) per_sm = want_per_sm;
     return per_sm * std::max(ctx->num_sms, 1);
+}
+
+// Per-call cell state of the batched path, one int buffer of n = n_cells:
+//   [0, 3n) cell lists of the three groups   [3n) candidates (N_p < N_t cells)
+//   [4n) coefficients                        [5n) cells with N_p < N_t candidates
+//   [6n) cells with events                   [7n) listed flags
+//   [8n, 10n) ledger contributions (float2)  [10n) class histograms and cursors,
+//   then three counters (flat queue, N_p < N_t cells, cells with events).
+// Flags and contributions start at zero and are cleared by the finalize kernel.
+static int ensure_lists(pcc_ctx* ctx, int n_cells)
+{
+    if (ctx->lists && ctx->lists_cells >= n_cells) return PCC_OK;
+    if (ctx->lists) cudaFree(ctx->lists);
+    ctx->lists = nullptr;
+    ctx->lists_cells = 0;
+    const size_t bytes = ((size_t)10 * n_cells + 6 * kClasses + 8) * sizeof(int);
+    cudaError_t e = cudaMalloc(&ctx->lists, bytes);
+    if (e == cudaSuccess) e = cudaMemset(ctx->lists, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: cell lists");
+    ctx->lists_cells = n_cells;
+    return PCC_OK;
+}
+
+static int ensure_queue(pcc_ctx* ctx, size_t cap_a, size_t cap_b)
+{
+    if (cap_a > ctx->queue_a_cap) {
+        if (ctx->queue_a) cudaFree(ctx->queue_a);
+        ctx->queue_a = nullptr;
+        ctx->queue_a_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->queue_a, cap_a * sizeof(uint2));
+        if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: candidate queue");
+        ctx->queue_a_cap = cap_a;
+    }
+    if (cap_b > ctx->queue_b_cap) {
+        if (ctx->queue_b) cudaFree(ctx->queue_b);
+        ctx->queue_b = nullptr;
+        ctx->queue_b_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->queue_b, cap_b * sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: candidate queue");
+        ctx->queue_b_cap = cap_b;
+    }
+    return PCC_OK;
+}
+
+static CellList list_of(pcc_ctx* ctx, int group)
+{
+    const size_t n = ctx->lists_cells;
+    CellList L;
+    L.list = ctx->lists + (size_t)group * n;
+    L.hist = ctx->lists + 10 * n + (size_t)(2 * group) * kClasses;
+    L.cursor = L.hist + kClasses;
+    return L;
+}
+
+static int* counters_of(pcc_ctx* ctx) { return ctx->lists + 10 * (size_t)ctx->lists_cells + 6 * kClasses; }
+
+static Queue queue_of(pcc_ctx* ctx)
+{
+    const size_t n = ctx->lists_cells;
+    int* c = counters_of(ctx);
+    Queue Q;
+    Q.flat = (uint2*)ctx->queue_a;
+    Q.cap_flat = (uint32_t)std::min<size_t>(ctx->queue_a_cap, 0xFFFFFFFFu);
+    Q.flat_count = c;
+    Q.qb = (uint32_t*)ctx->queue_b;
+    Q.cand = ctx->lists + 3 * n;
+    Q.coef = reinterpret_cast<float*>(ctx->lists + 4 * n);
+    Q.caseb = ctx->lists + 5 * n;
+    Q.caseb_count = c + 1;
+    Q.flagged = ctx->lists + 6 * n;
+    Q.flagged_count = c + 2;
+    Q.flag = ctx->lists + 7 * n;
+    Q.evacc = reinterpret_cast<float2*>(ctx->lists + 8 * n);
+    return Q;
+}
+
+template <int GROUP, int MINB>
+static void launch_scan(pcc_ctx* ctx, const StepArgs& a, const CellList& L, const Queue& Q, cudaStream_t st)
+{
+    const int g = persistent_grid(ctx, (const void*)scan_kernel<GROUP, MINB>, 0, ctx->blocks_per_sm);
+    scan_kernel<GROUP, MINB><<<g, kBatchedThreads, 0, st>>>(a, L, Q);
+}
+
+// Per group: counters, size classes, scan (register budget chosen by the
+// schedule: 2, 3 or 4 resident blocks per SM), candidates, finalize.
+template <int GROUP>
+static cudaError_t launch_batched(pcc_ctx* ctx, const StepArgs& a, const SpeciesView& P, int stage, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(counters_of(ctx), 0, 3 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const CellList L = list_of(ctx, GROUP);
+    const Queue Q = queue_of(ctx);
+    const int blocks = (a.n_cells + 255) / 256;
+    class_hist_kernel<<<blocks, 256, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
+    class_scatter_kernel<<<blocks, 256, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
+    if (ctx->minb == 2) launch_scan<GROUP, 2>(ctx, a, L, Q, st);
+    else if (ctx->minb == 3) launch_scan<GROUP, 3>(ctx, a, L, Q, st);
+    else launch_scan<GROUP, 4>(ctx, a, L, Q, st);
+    const int gf = persistent_grid(ctx, (const void*)flat_cand_kernel<GROUP>, stage, 0);
+    flat_cand_kernel<GROUP><<<gf, kBatchedThreads, stage, st>>>(a, Q, stage);
+    const int gb = persistent_grid(ctx, (const void*)caseb_cand_kernel<GROUP>, stage, 0);
+    caseb_cand_kernel<GROUP><<<gb, kBatchedThreads, stage, st>>>(a, Q, stage);
+    finalize_kernel<GROUP><<<2 * std::max(ctx->num_sms, 1), 256, 0, st>>>(a, Q);
+    return cudaSuccess;
+}
+
+extern "C" int pcc_set_schedule(pcc_ctx* ctx, int min_blocks_per_sm, int blocks_per_sm)
+{
+    if (!ctx || min_blocks_per_sm < 2 || min_blocks_per_sm > 4 || blocks_per_sm < 0) {
+        set_error("pcc_set_schedule: invalid schedule");
+        return PCC_E_INVALID;
+    }
+    ctx->minb = min_blocks_per_sm;
+    ctx->blocks_per_sm = blocks_per_sm;
+    return PCC_OK;
 }
 
 extern "C" int pcc_collide(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em, pcc_species* ep, pcc_species* ph,
@@ -794,17 +1637,23 @@ extern "C" int pcc_collide(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em
         if (run_ep) collide_plain_kernel<kGroupEp><<<cells->n_cells, 128, 0, st>>>(a);
         if (run_ph) collide_plain_kernel<kGroupPh><<<cells->n_cells, 128, 0, st>>>(a);
     } else {
+        int rc = ensure_lists(ctx, cells->n_cells);
+        if (rc) return rc;
+        size_t cap_a = 0;
+        if (run_em) cap_a = std::max(cap_a, (size_t)em->capacity);
+        if (run_ep) cap_a = std::max(cap_a, (size_t)ep->capacity);
+        if (run_ph) cap_a = std::max(cap_a, (size_t)ph->capacity);
+        rc = ensure_queue(ctx, std::max<size_t>(cap_a, 1), std::max<size_t>((size_t)ion->capacity, 1));
+        if (rc) return rc;
+        // zero the class histograms and cursors of the three groups (see list_of)
+        cudaError_t e = cudaMemsetAsync(ctx->lists + 10 * (size_t)ctx->lists_cells, 0, 6 * kClasses * sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: list counters");
         const size_t tab_bytes = (size_t)ctx->n_mat * ctx->spec.n_rows * sizeof(float);
         const int stage = (tab_bytes % 16 == 0 && tab_bytes <= 48 * 1024) ? (int)tab_bytes : 0;
-        if (run_em || run_ep) {
-            const int g = batched_grid(ctx, (const void*)collide_batched_kernel<kGroupEm>, stage);
-            if (run_em) collide_batched_kernel<kGroupEm><<<g, kBatchedThreads, stage, st>>>(a, stage);
-            if (run_ep) collide_batched_kernel<kGroupEp><<<g, kBatchedThreads, stage, st>>>(a, stage);
-        }
-        if (run_ph) {
-            const int g = batched_grid(ctx, (const void*)collide_batched_kernel<kGroupPh>, stage);
-            collide_batched_kernel<kGroupPh><<<g, kBatchedThreads, stage, st>>>(a, stage);
-        }
+        if (run_em && e == cudaSuccess) e = launch_batched<kGroupEm>(ctx, a, a.em, stage, st);
+        if (run_ep && e == cudaSuccess) e = launch_batched<kGroupEp>(ctx, a, a.ep, stage, st);
+        if (run_ph && e == cudaSuccess) e = launch_batched<kGroupPh>(ctx, a, a.ph, stage, st);
+        if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: batched launch");
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PCC_OK : cuda_fail(e, "pcc_collide: launch");

@@ -61,6 +61,38 @@ __device__ __forceinline__ Philox4 draw(uint32_t c0, uint32_t cell, uint64_t ste
     return philox4x32_10(c0, cell, (uint32_t)step, tag, (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
+// The same generator with the ten round keys precomputed (key schedule of
+// Philox4x32-10: k0 + r 0x9E3779B9, k1 + r 0xBB67AE85), so that a kernel can
+// read them from its parameter space instead of keeping them in registers.
+struct PhiloxKeys { uint32_t k0[10], k1[10]; };
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint64_t seed)
+{
+    PhiloxKeys K;
+    uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = a;
+        K.k1[r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return K;
+}
+
+__device__ __forceinline__ Philox4 draw_k(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const PhiloxKeys& K)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ K.k0[r], n2 = hi0 ^ c3 ^ K.k1[r];
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    Philox4 o;
+    o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+    return o;
+}
+
 // ---------------------------------------------------------------------------
 // Pairing permutation P on [0, n) for the larger list of a cell.
 //   n <= 32: P^-1(s) = rank of s under keys mix(mix(s, k0), k1) (ties by s).
@@ -162,6 +194,7 @@ struct DevStats {
     unsigned long long created[5];
     double energy_change;
     double charge_change;
+    unsigned long long candidates[3];
 };
 
 __device__ __forceinline__ void raise_status(DevStats* st, unsigned bits) { atomicOr(&st->status, bits); }

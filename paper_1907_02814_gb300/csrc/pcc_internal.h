@@ -28,11 +28,22 @@ struct pcc_ctx {
     float* f_tri_gp_cdf = nullptr;
     float* f_tri_split_cdf = nullptr;
     float* f_Z = nullptr;             // [n_mat] nuclear charge as float
+    float* f_bound = nullptr;         // [n_mat][3] acceptance bounds: Brems, Trident, BH
     // status and counters
     pcc::DevStats* stats = nullptr;
     // scratch
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    // cell work lists of the batched collision kernels (3 groups + class counters)
+    int* lists = nullptr;
+    int lists_cells = 0;
+    // launch schedule of the batched kernels (set by pcc_tune or defaults)
+    void* queue_a = nullptr;       // candidate queue over projectile slots
+    size_t queue_a_cap = 0;
+    void* queue_b = nullptr;       // candidate queue over target slots (N_p < N_t cells)
+    size_t queue_b_cap = 0;
+    int minb = 4;                  // register budget: minimum resident blocks per SM
+    int blocks_per_sm = 0;         // persistent grid cap (0: as many as fit)
 };
 
 namespace pcc {

@@ -176,6 +176,38 @@ __global__ void z_to_float_kernel(const double* screen, float* out, int n)
     if (i < n) out[i] = (float)screen[(size_t)i * kScreenFields + 7];
 }
 
+// Per-material upper bounds B with x <= coef * B for every pair (coef =
+// (n_p n_t / n_pt) c dt), used to reject a pair from its uniform alone:
+//   Brems:   x = coef sigma(T') p'/(g_e g_i) <= coef sigma(T') beta' (1 + |beta_i|),
+//            and the log-log interpolated sigma between rows j, j+1 is at most
+//            max(sigma_j, sigma_j+1) while beta' <= beta(T_j+1); the last row
+//            covers energies above the table.
+//   Trident: sigma_T is increasing in gamma; the bound holds for gamma' <= 1e7.
+//   BH:      x = coef sigma(k') k'/(k g_i) <= coef sigma(k') (1 + |beta_i|).
+// The factor 2 covers 1 + |beta_i|; 1e-3 more covers float rounding of x.
+__global__ void bounds_kernel(const double* screen, const double* brems_sigma, const double* bh_sigma, TableGeom g,
+                              int n_mat, float* bound)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_mat) return;
+    const double* sb = brems_sigma + (size_t)m * g.n_rows;
+    const double* sh = bh_sigma + (size_t)m * g.n_rows;
+    double bb = sb[g.n_rows - 1], bh = 0.0;
+    for (int j = 0; j + 1 < g.n_rows; ++j) {
+        const double T = g.T_min * pow(g.T_max / g.T_min, (double)(j + 1) / (g.n_rows - 1));
+        const double beta = sqrt(T * (T + 2.0)) / (1.0 + T);
+        bb = fmax(bb, fmax(sb[j], sb[j + 1]) * beta);
+    }
+    for (int j = 0; j < g.n_rows; ++j) bh = fmax(bh, sh[j]);
+    const double Z = screen[(size_t)m * kScreenFields + 7];
+    const double l = log((1e7 + 4.5) / 6.89);
+    const double bt = 5.22e-34 * Z * Z * l * l * l;
+    const double margin = 2.0 * 1.001;
+    bound[3 * m + 0] = (float)(margin * bb);
+    bound[3 * m + 1] = (float)(margin * bt);
+    bound[3 * m + 2] = (float)(margin * bh);
+}
+
 }  // namespace pcc
 
 using namespace pcc;
@@ -184,13 +216,13 @@ static void free_tables(pcc_ctx* ctx)
 {
     void* ptrs[] = {ctx->screen, ctx->brems_sigma, ctx->brems_cdf, ctx->bh_sigma, ctx->bh_cdf, ctx->tri_gp_cdf,
                     ctx->tri_split_cdf, ctx->f_brems_lnsig, ctx->f_brems_cdf, ctx->f_bh_lnsig, ctx->f_bh_cdf,
-                    ctx->f_tri_gp_cdf, ctx->f_tri_split_cdf, ctx->f_Z};
+                    ctx->f_tri_gp_cdf, ctx->f_tri_split_cdf, ctx->f_Z, ctx->f_bound};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ctx->screen = ctx->brems_sigma = ctx->brems_cdf = ctx->bh_sigma = ctx->bh_cdf = nullptr;
     ctx->tri_gp_cdf = ctx->tri_split_cdf = nullptr;
     ctx->f_brems_lnsig = ctx->f_brems_cdf = ctx->f_bh_lnsig = ctx->f_bh_cdf = nullptr;
-    ctx->f_tri_gp_cdf = ctx->f_tri_split_cdf = ctx->f_Z = nullptr;
+    ctx->f_tri_gp_cdf = ctx->f_tri_split_cdf = ctx->f_Z = ctx->f_bound = nullptr;
     ctx->n_mat = 0;
 }
 
@@ -235,6 +267,7 @@ extern "C" int pcc_tables_build(pcc_ctx* ctx, const pcc_material* mats, int n_ma
     A((void**)&ctx->f_tri_gp_cdf, R * C * sizeof(float));
     A((void**)&ctx->f_tri_split_cdf, R * C * sizeof(float));
     A((void**)&ctx->f_Z, M * sizeof(float));
+    A((void**)&ctx->f_bound, 3 * M * sizeof(float));
     if (e != cudaSuccess) { free_tables(ctx); return cuda_fail(e, "pcc_tables_build: cudaMalloc"); }
 
     pcc_material* dmats = nullptr;
@@ -269,6 +302,8 @@ extern "C" int pcc_tables_build(pcc_ctx* ctx, const pcc_material* mats, int n_ma
     conv(ctx->tri_gp_cdf, ctx->f_tri_gp_cdf, R * C, 0);
     conv(ctx->tri_split_cdf, ctx->f_tri_split_cdf, R * C, 0);
     z_to_float_kernel<<<(n_mats + 63) / 64, 64, 0, st>>>(ctx->screen, ctx->f_Z, n_mats);
+    bounds_kernel<<<(n_mats + 63) / 64, 64, 0, st>>>(ctx->screen, ctx->brems_sigma, ctx->bh_sigma, g, n_mats,
+                                                     ctx->f_bound);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(dmats);

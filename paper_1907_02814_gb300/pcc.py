@@ -53,7 +53,7 @@ class Cells(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("pairs", C.c_ulonglong * 3), ("accepted", C.c_ulonglong * 5), ("created", C.c_ulonglong * 5),
-                ("energy_change", C.c_double), ("charge_change", C.c_double)]
+                ("energy_change", C.c_double), ("charge_change", C.c_double), ("candidates", C.c_ulonglong * 3)]
 
 
 _lib = None
@@ -69,6 +69,7 @@ EXPORTS = {
     "pcc_collide": (C.c_int, [_vp, C.POINTER(Cells), C.POINTER(Species), C.POINTER(Species), C.POINTER(Species),
                               C.POINTER(Species), C.c_double, C.c_uint64, C.c_uint64, C.c_uint, C.c_int, _vp, _vp]),
     "pcc_append_secondaries": (C.c_int, [_vp, C.c_int, C.POINTER(Species), _vp]),
+    "pcc_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
     "pcc_pairing": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.POINTER(Species), C.c_int, C.c_uint64,
                               C.c_uint64, _vp, _vp, _vp]),
     "pcc_totals": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.c_int, _vp, _vp]),
@@ -166,12 +167,16 @@ class Context:
                "pcc_tables_read")
         return out
 
+    def set_schedule(self, min_blocks_per_sm=4, blocks_per_sm=0):
+        _check(self.lib.pcc_set_schedule(self.h, int(min_blocks_per_sm), int(blocks_per_sm)), "pcc_set_schedule")
+
     def read_status(self, stream=None):
         st = C.c_uint(0)
         s = Stats()
         _check(self.lib.pcc_read_status(self.h, C.byref(st), C.byref(s), _stream(stream)), "pcc_read_status")
         return st.value, {"pairs": list(s.pairs), "accepted": list(s.accepted), "created": list(s.created),
-                          "energy_change": s.energy_change, "charge_change": s.charge_change}
+                          "energy_change": s.energy_change, "charge_change": s.charge_change,
+                          "candidates": list(s.candidates)}
 
 
 @dataclass
