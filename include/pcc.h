@@ -222,6 +222,21 @@ int pcc_pairing(pcc_ctx *ctx, int n_cells, const pcc_species *proj, const pcc_sp
 int pcc_totals(pcc_ctx *ctx, int n_cells, const pcc_species *sp, int is_photon, double *out,
                void *stream);
 
+/* Allocation-free variant of pcc_totals (no counterpart in the paper; a
+ * service for callers that may not allocate device memory while they run,
+ * such as a simulation that sizes all its buffers at start-up, an
+ * application whose own allocator owns the device, or a step being recorded
+ * into a CUDA graph).  Same result as pcc_totals up to the order of the FP64
+ * sums; needs no context.  Its scratch is a fixed 96 KiB array in the
+ * library's device memory (held by every GPU that loads the library until
+ * the process exits), so n_cells is limited to 4,194,304: larger counts
+ * return PCC_E_CAPACITY without launching anything.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Calls share the array: two
+ * calls whose kernels can run at the same time (unordered streams) race.
+ * out: device double[3].  Asynchronous after the first call. */
+int pcc_totals_noalloc(int n_cells, const pcc_species *sp, int is_photon, double *out, void *stream);
+
 /* Read and clear the device status word and step counters.  Synchronises
  * the stream.  status_out: PCC_ST_* bits; stats_out may be NULL. */
 int pcc_read_status(pcc_ctx *ctx, unsigned *status_out, pcc_stats *stats_out, void *stream);

@@ -73,6 +73,7 @@ EXPORTS = {
     "pcc_pairing": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.POINTER(Species), C.c_int, C.c_uint64,
                               C.c_uint64, _vp, _vp, _vp]),
     "pcc_totals": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.c_int, _vp, _vp]),
+    "pcc_totals_noalloc": (C.c_int, [C.c_int, C.POINTER(Species), C.c_int, _vp, _vp]),
     "pcc_read_status": (C.c_int, [_vp, C.POINTER(C.c_uint), C.POINTER(Stats), _vp]),
     "pcc_expected_emission_fwd": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "pcc_expected_emission_bwd": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp,
@@ -276,6 +277,14 @@ def totals(ctx: Context, n_cells, sp: DeviceSpecies, is_photon=False, stream=Non
     s = sp.cstruct()
     _check(ctx.lib.pcc_totals(ctx.h, int(n_cells), C.byref(s), int(bool(is_photon)), _ptr(out), _stream(stream)),
            "pcc_totals")
+    return out
+
+
+def totals_noalloc(n_cells, sp: DeviceSpecies, out, is_photon=False, stream=None):
+    """Allocation-free totals into the caller's device double[3] `out`."""
+    s = sp.cstruct()
+    _check(load().pcc_totals_noalloc(int(n_cells), C.byref(s), int(bool(is_photon)), _ptr(out), _stream(stream)),
+           "pcc_totals_noalloc")
     return out
 
 
