@@ -114,6 +114,7 @@ def lib():
                                    C.POINTER(Stats)]
             L.orc_boost.argtypes = [_dp, _dp, _dp, C.c_int]
             L.orc_expected_emission.argtypes = [C.POINTER(Material), C.c_int, _dp, _dp, C.c_int, _dp]
+            L.orc_expected_emission_grad.argtypes = [C.POINTER(Material), C.c_int, _dp, _dp, C.c_int, _dp, _dp]
     return _lib
 
 
@@ -344,3 +345,15 @@ def expected_emission(mat: Material, gamma, w, n_quad=64):
     lib().orc_expected_emission(C.byref(mat), len(g), g.ctypes.data_as(_dp), ww.ctypes.data_as(_dp),
                                 int(n_quad), out.ctypes.data_as(_dp))
     return out
+
+
+def expected_emission_grad(mat: Material, gamma, w, g_out, n_quad=64):
+    """sum_j g_out[j] d out[j] / d (n_i, T_e, Z*, s_TF, s_D), FP64."""
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    go = np.ascontiguousarray(g_out, dtype=np.float64)
+    out = np.zeros(5)
+    lib().orc_expected_emission_grad(C.byref(mat), len(g), g.ctypes.data_as(_dp), ww.ctypes.data_as(_dp),
+                                     int(n_quad), go.ctypes.data_as(_dp), out.ctypes.data_as(_dp))
+    return out
+

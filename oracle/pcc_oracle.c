@@ -1024,3 +1024,33 @@ void orc_expected_emission(const orc_material *m, int n_samples, const double *g
     out3[1] = m->n_i * Rp;
     out3[2] = m->n_i * P;
 }
+
+/* Gradient of the expected-emission operator with respect to the plasma
+ * parameters theta = (n_i, T_e, Z*, s_TF, s_D), contracted with g_out:
+ *   grad[k] = sum_j g_out[j] d out[j] / d theta_k.
+ * By the definition of the derivative: central differences of the FP64
+ * operator with relative step h = 1e-3 theta_k, Richardson-extrapolated from
+ * steps h and h/2 (error O(h^4)).  Valid away from the kink of
+ * max(lambda_D, r_i). */
+void orc_expected_emission_grad(const orc_material *m, int n_samples, const double *gamma,
+                                const double *w, int n_quad, const double *g_out, double *grad)
+{
+    for (int k = 0; k < 5; ++k) {
+        double D[2];
+        for (int r = 0; r < 2; ++r) {
+            orc_material lo = *m, hi = *m;
+            double *plo[5] = { &lo.n_i, &lo.T_e, &lo.Zstar, &lo.s_TF, &lo.s_D };
+            double *phi[5] = { &hi.n_i, &hi.T_e, &hi.Zstar, &hi.s_TF, &hi.s_D };
+            double h = 1e-3 * fabs(*plo[k]) / (r == 0 ? 1.0 : 2.0);
+            *plo[k] -= h;
+            *phi[k] += h;
+            double olo[3], ohi[3];
+            orc_expected_emission(&lo, n_samples, gamma, w, n_quad, olo);
+            orc_expected_emission(&hi, n_samples, gamma, w, n_quad, ohi);
+            D[r] = 0.0;
+            for (int j = 0; j < 3; ++j) D[r] += g_out[j] * (ohi[j] - olo[j]) / (2.0 * h);
+        }
+        grad[k] = (4.0 * D[1] - D[0]) / 3.0;
+    }
+}
+

@@ -132,6 +132,8 @@ int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
 /* ---- expected-emission operator (Eq. N_br_theo1/2 rate form) ---- */
 void orc_expected_emission(const orc_material *m, int n_samples, const double *gamma,
                            const double *w, int n_quad, double *out3);
+void orc_expected_emission_grad(const orc_material *m, int n_samples, const double *gamma,
+                                const double *w, int n_quad, const double *g_out, double *grad5);
 
 #ifdef __cplusplus
 }
