@@ -48,35 +48,91 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and throttle reasons sampled during the timed region: NVML
+    (every 5 ms) when the driver library can be opened, else nvidia-smi
+    (every 100 ms).  Reads only; changes no setting."""
+    SW_POWER_CAP, HW_SLOWDOWN, SW_THERMAL, HW_THERMAL = 0x4, 0x8, 0x20, 0x40
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.rows = []
-        self.proc = None
+    def __init__(self, cuda_index, period_s=0.005):
+        self.cuda_index = cuda_index
+        self.period = period_s
+        self.rows = []          # (sm_mhz, reason bits)
+        self.max_mhz = None
+        self.source = None
+        self._stop = threading.Event()
         self.thread = None
+        self.proc = None
+
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        import torch
+        p = torch.cuda.get_device_properties(self.cuda_index)
+        tries = []
+        uuid = getattr(p, "uuid", None)
+        if uuid is not None:
+            tries.append(("nvmlDeviceGetHandleByUUID", f"GPU-{uuid}".encode()))
+        if hasattr(p, "pci_bus_id"):
+            bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0".encode()
+            tries.append(("nvmlDeviceGetHandleByPciBusId_v2", bus))
+        for fn, arg in tries:
+            if getattr(lib, fn)(ctypes.c_char_p(arg), ctypes.byref(h)) == 0:
+                return lib, h
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.cuda_index), ctypes.byref(h)) == 0:
+            return lib, h
+        raise OSError("no NVML handle for this device")
 
     def start(self):
+        import ctypes
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
-                                         stderr=subprocess.DEVNULL, text=True)
-        except (OSError, FileNotFoundError):
-            self.proc = None
+            lib, h = self._nvml_handle()
+            reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint(0)
+            if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            self.source = "nvml"
+
+            def loop():
+                c, r = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+                while not self._stop.is_set():
+                    if lib.nvmlDeviceGetClockInfo(h, ctypes.c_int(1), ctypes.byref(c)) == 0 and \
+                            reasons_fn(h, ctypes.byref(r)) == 0:
+                        self.rows.append((float(c.value), int(r.value)))
+                    time.sleep(self.period)
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
             return
-        self.thread = threading.Thread(target=self._read, daemon=True)
+        except (OSError, AttributeError):
+            pass
+        self._start_smi()
+
+    def _start_smi(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.cuda_index), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
+        self.source = "nvidia-smi"
+        bits = (self.HW_SLOWDOWN, self.HW_THERMAL, self.SW_THERMAL, self.SW_POWER_CAP)
+
+        def read():
+            for line in self.proc.stdout:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 6 and f[0].replace(".", "").isdigit():
+                    self.max_mhz = float(f[1]) if f[1].replace(".", "").isdigit() else self.max_mhz
+                    self.rows.append((float(f[0]), sum(b for b, v in zip(bits, f[2:6]) if v == "Active")))
+        self.thread = threading.Thread(target=read, daemon=True)
         self.thread.start()
 
-    def _read(self):
-        for line in self.proc.stdout:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append(parts)
-
     def stop(self):
+        self._stop.set()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -85,12 +141,12 @@ class ClockSampler:
                 self.proc.kill()
         if self.thread is not None:
             self.thread.join(timeout=5)
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].strip() == "Active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+        names = {self.HW_SLOWDOWN: "hw_slowdown", self.HW_THERMAL: "hw_thermal_slowdown",
+                 self.SW_THERMAL: "sw_thermal_slowdown", self.SW_POWER_CAP: "sw_power_cap"}
+        reasons = sorted({n for _, r in self.rows for b, n in names.items() if r & b})
+        sm = [c for c, _ in self.rows]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(self.rows), "source": self.source}
 
 
 def source_hash():
@@ -121,6 +177,11 @@ def profiled_traffic(kernel_tag):
         return None
 
 
+# Cell-region slack (absolute, relative) per species: room for the
+# secondaries that the warm-up and timed steps append.
+SLACK = {"em": (8, 0.05), "ep": (16, 0.0), "ph": (32, 0.3), "ion": (0, 0.0)}
+
+
 # ------------------------------------------------------------------ setup --
 def setup(ctx, pcc, W, torch, counts, slack):
     mat = counts["material"]
@@ -148,17 +209,25 @@ def live_counts(dev, torch):
     return {k: int(v.cell_count.sum().item()) for k, v in dev.items()}
 
 
-def ei_pairs_and_bytes(dev, torch):
-    """Pairs and algorithmic bytes of the electron-ion launch: 16 B per
-    projectile and per target record of every cell with both, plus 20 B of
-    per-cell metadata (starts, counts, material)."""
-    ce = dev["em"].cell_count.long()
-    ci = dev["ion"].cell_count.long()
-    both = (ce > 0) & (ci > 0)
-    pairs = int(torch.where(both, torch.maximum(ce, ci), torch.zeros_like(ce)).sum().item())
-    recs = int((ce[both].sum() + ci[both].sum()).item())
-    n_cells = ce.numel()
-    return pairs, 16 * recs + 20 * n_cells
+# Algorithmic bytes (minimum traffic of the method, FP32 state): a particle
+# record is u (12 B) + W (4 B) + id (8 B) = 24 B; per cell, a start and a
+# count (8 B) of every species read, the material id (4 B) and the
+# 16-byte ledger; writes of 12 B per changed projectile and 32 B per
+# secondary (record + id).
+REC_B, CELL_SPECIES_B, CELL_FIXED_B, CHANGED_B, SECONDARY_B = 24, 8, 20, 12, 32
+
+
+def ei_bytes(live, n_cells, changed, secondaries):
+    """One electron-ion collide launch: every electron and ion record."""
+    return (REC_B * (live["em"] + live["ion"]) + (2 * CELL_SPECIES_B + CELL_FIXED_B) * n_cells
+            + CHANGED_B * changed + SECONDARY_B * secondaries)
+
+
+def step_bytes(live, n_cells, changed, secondaries):
+    """One full step: the records of every species, the cell metadata of all
+    four species, and the writes."""
+    return (REC_B * (live["em"] + live["ep"] + live["ph"] + live["ion"])
+            + (4 * CELL_SPECIES_B + CELL_FIXED_B) * n_cells + CHANGED_B * changed + SECONDARY_B * secondaries)
 
 
 def run_gpu(args):
@@ -166,6 +235,7 @@ def run_gpu(args):
     import torch.distributed as dist
 
     from paper_1907_02814_gb300 import build, pcc
+    from paper_1907_02814_gb300 import tune as tuner
     from paper_1907_02814_gb300 import workloads as W
 
     rank, world, local = dist_env()
@@ -177,54 +247,55 @@ def run_gpu(args):
     ctx = pcc.Context(local)
     counts = W.batched_cu(seed=3 + rank)
     n_cells = len(counts["e"])
-    slack = {"em": (4, 0.02), "ep": (6, 0.0), "ph": (8, 0.05), "ion": (0, 0.0)}
-    dev = setup(ctx, pcc, W, torch, counts, slack)
+    dev = setup(ctx, pcc, W, torch, counts, SLACK)
     mat_of_cell = torch.zeros(n_cells, dtype=torch.int32, device="cuda")
     ledger = torch.zeros((n_cells, 4), dtype=torch.float32, device="cuda")
     prec = pcc.FP32_BATCHED if args.precision == "fp32" else pcc.FP64_PLAIN
     stream = torch.cuda.current_stream()
     dt, seed = counts["dt"], counts["seed"]
     ion_mass = counts["ion_mass"]
-    launches_per_step = 6
+    mask = pcc.BREMS | pcc.TRIDENT | pcc.BH
 
-    def step(s, ev=None):
-        if ev is not None:
-            ev[0].record(stream)
+    schedule = None
+    if prec == pcc.FP32_BATCHED and not args.no_tune:
+        schedule = tuner.tune(ctx, pcc, torch, n_cells, mat_of_cell, ion_mass, dev, dt, seed, step=90_000)
+
+    def eager_step(s):
         pcc.collide(ctx, n_cells, mat_of_cell, ion_mass, dev["em"], dev["ep"], dev["ph"], dev["ion"], dt, seed, s,
-                    mask=pcc.BREMS | pcc.TRIDENT | pcc.GROUP_EM, precision=prec, ledger=ledger)
-        if ev is not None:
-            ev[1].record(stream)
-        pcc.collide(ctx, n_cells, mat_of_cell, ion_mass, dev["em"], dev["ep"], dev["ph"], dev["ion"], dt, seed, s,
-                    mask=pcc.BREMS | pcc.TRIDENT | pcc.BH | pcc.GROUP_EP | pcc.GROUP_PH, precision=prec,
-                    ledger=ledger)
+                    mask=mask, precision=prec, ledger=ledger)
         for k in ("em", "ep", "ph"):
             pcc.append_secondaries(ctx, n_cells, dev[k])
 
     for s in range(args.warmup):
-        step(s)
+        eager_step(s)
+    torch.cuda.synchronize()
+    # the K timed steps as one CUDA graph, with events around each part of each step
+    ctx.steps_capture(n_cells, mat_of_cell, ion_mass, dev["em"], dev["ep"], dev["ph"], dev["ion"], dt, seed,
+                      step0=args.warmup, n_steps=args.steps, mask=mask, precision=prec, ledger=ledger, timing=True)
     torch.cuda.synchronize()
     ctx.read_status()
-    pairs_ei, bytes_ei = ei_pairs_and_bytes(dev, torch)
     before = live_counts(dev, torch)
 
     clocks = ClockSampler(local)
     clocks.start()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    time.sleep(0.05)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = pcc.launch_count()
     start.record(stream)
-    for s in range(args.steps):
-        step(args.warmup + s, evs[s])
+    ctx.steps_launch()
     end.record(stream)
+    launches = pcc.launch_count() - launches0
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     ms = start.elapsed_time(end)
-    ei_ms = [a.elapsed_time(b) for a, b in evs]
+    parts = ctx.steps_timing()            # [K][EI, EP, PH, commit] ms
     status, stats = ctx.read_status()
+    after = live_counts(dev, torch)
     pairs = sum(stats["pairs"])
     events = sum(stats["created"])
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -239,26 +310,42 @@ def run_gpu(args):
     e2e = e2e_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, seed, prec)
 
     peak, peak_kind = peaks()
-    ei_avg = float(np.mean(ei_ms))
-    achieved = bytes_ei / (ei_avg * 1e-3) / 1e9
-    traffic = profiled_traffic("collide_ei_batched" if prec == pcc.FP32_BATCHED else "collide_ei_plain")
+    K = args.steps
+    avg_live = {k: 0.5 * (before[k] + after[k]) for k in before}
+    cr = stats["created"]                 # Brems e-, Brems e+, Trident e-, Trident e+, BH
+    ei_changed = (cr[0] + cr[2]) / K
+    ei_secondaries = (cr[0] + 2 * cr[2]) / K
+    all_changed = (cr[0] + cr[1] + cr[2] + cr[3]) / K
+    all_secondaries = (cr[0] + cr[1] + 2 * (cr[2] + cr[3] + cr[4])) / K
+    b_ei = ei_bytes(avg_live, n_cells, ei_changed, ei_secondaries)
+    b_step = step_bytes(avg_live, n_cells, all_changed, all_secondaries)
+    ei_ms = float(np.mean(parts[:, 0]))
+    step_ms = ms_max / K
+    achieved = b_ei / (ei_ms * 1e-3) / 1e9
+    achieved_step = b_step / (step_ms * 1e-3) / 1e9
+    tag = "collide_ei_batched" if prec == pcc.FP32_BATCHED else "collide_ei_plain"
     result = {
         "metric": METRIC, "value": pairs_all / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "steps": K, "warmup": args.warmup, "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == pcc.FP32_BATCHED else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": n_cells, "electrons": before["em"], "ions": before["ion"],
                    "photons": before["ph"], "positrons": before["ep"], "precision": args.precision,
-                   "l2": "inputs larger than L2 (about 6 GB of particle records per step)",
+                   "l2": "inputs larger than L2 (about 7 GB of particle records), no flush",
+                   "timed": f"{K} steps in one CUDA graph", "schedule": schedule and list(schedule["schedule"]),
                    "parallelism": f"replicas{world}"},
         "events_per_s": events_all / (ms_max * 1e-3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "collide electron-ion (Brems+Trident) batched" if prec == pcc.FP32_BATCHED
-                     else "collide electron-ion plain FP64",
-                     "bytes_per_launch": bytes_ei, "ms_per_launch": ei_avg, "peak_kind": peak_kind},
+                     "frac": achieved / peak, "traffic": profiled_traffic(tag),
+                     "kernel": "pcc_collide electron-ion group (Brems + Trident), "
+                               + ("batched FP32" if prec == pcc.FP32_BATCHED else "plain FP64"),
+                     "bytes_per_launch": b_ei, "ms_per_launch": ei_ms, "peak_kind": peak_kind},
+        "roofline_step": {"bound": "hbm", "achieved": achieved_step, "peak": peak, "unit": "GB/s",
+                          "frac": achieved_step / peak, "bytes_per_step": b_step,
+                          "ms_parts": {"ei": ei_ms, "ep": float(np.mean(parts[:, 1])),
+                                       "ph": float(np.mean(parts[:, 2])), "commit": float(np.mean(parts[:, 3]))}},
         "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": int(launches),
         "clocks": clk,
         "status": status,
     }
@@ -364,12 +451,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

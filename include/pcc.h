@@ -237,6 +237,42 @@ int pcc_totals(pcc_ctx *ctx, int n_cells, const pcc_species *sp, int is_photon, 
  * out: device double[3].  Asynchronous after the first call. */
 int pcc_totals_noalloc(int n_cells, const pcc_species *sp, int is_photon, double *out, void *stream);
 
+/* The multi-step collision loop as one CUDA graph (the batching pattern
+ * around Sec. III.A's per-step procedure).  One captured step is:
+ * pcc_collide for each group of the mask in the order e-, e+, photons
+ * (each as its own call with the matching PCC_GROUP_* bit), then
+ * pcc_append_secondaries for e-, e+ and photons.  pcc_steps_capture records
+ * n_steps such steps, for step indices step0 .. step0 + n_steps - 1, into a
+ * graph owned by the context (replacing any earlier one); every allocation
+ * the steps need happens before the capture, which runs on a stream of the
+ * context's own, so the caller's stream is not captured.  All pointers in
+ * the descriptor must stay valid and unchanged while the graph is used.
+ * timing != 0 adds five timing events per step (before the e- group, after
+ * each group, after the commits), read by pcc_steps_timing.
+ * pcc_steps_launch enqueues the whole graph on the stream.  A launch
+ * repeats the same step indices: capture again to go on. */
+typedef struct {
+    const pcc_cells *cells;
+    pcc_species *em, *ep, *ph;
+    const pcc_species *ion;
+    double dt;
+    uint64_t seed;
+    unsigned mask;          /* PCC_BREMS | PCC_TRIDENT | PCC_BH [| group bits] */
+    int precision;          /* pcc_precision */
+    float *ledger;          /* device [n_cells][4] or NULL, as for pcc_collide */
+} pcc_step_desc;
+
+int pcc_steps_capture(pcc_ctx *ctx, const pcc_step_desc *desc, uint64_t step0, int n_steps, int timing,
+                      void *stream);
+int pcc_steps_launch(pcc_ctx *ctx, void *stream);
+/* After a launch: ms_out[n_steps][4] = e- group, e+ group, photon group,
+ * commits, in milliseconds (waits for the launch to finish). */
+int pcc_steps_timing(pcc_ctx *ctx, float *ms_out);
+
+/* Number of kernels the library has enqueued in this process (a graph
+ * launch counts each kernel node of the graph; capturing counts nothing). */
+unsigned long long pcc_launch_count(void);
+
 /* Read and clear the device status word and step counters.  Synchronises
  * the stream.  status_out: PCC_ST_* bits; stats_out may be NULL. */
 int pcc_read_status(pcc_ctx *ctx, unsigned *status_out, pcc_stats *stats_out, void *stream);

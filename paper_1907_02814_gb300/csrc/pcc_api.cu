@@ -1,4 +1,5 @@
 // Context lifetime, status readback and error reporting of the C ABI.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -8,6 +9,10 @@
 namespace pcc {
 
 static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -39,6 +44,8 @@ extern "C" const char* pcc_version(void) { return "pcc 0.1 (sm_103a)"; }
 
 extern "C" const char* pcc_last_error(void) { return g_last_error.c_str(); }
 
+extern "C" unsigned long long pcc_launch_count(void) { return launches_so_far(); }
+
 extern "C" int pcc_create(pcc_ctx** out, int device)
 {
     if (!out) { set_error("pcc_create: null output"); return PCC_E_INVALID; }
@@ -62,6 +69,8 @@ extern "C" int pcc_create(pcc_ctx** out, int device)
 extern "C" void pcc_destroy(pcc_ctx* ctx)
 {
     if (!ctx) return;
+    pcc_free_graph(ctx);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     pcc_free_tables(ctx);
     if (ctx->stats) cudaFree(ctx->stats);
     if (ctx->scratch) cudaFree(ctx->scratch);

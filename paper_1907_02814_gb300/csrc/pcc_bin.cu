@@ -283,12 +283,15 @@ extern "C" int pcc_bin(pcc_ctx* ctx, const pcc_particles* in, int n_cells, pcc_s
     if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, n_cells * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(tm, 0, 2 * sizeof(long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "pcc_bin: memset");
-    if (in->n > 0)
+    if (in->n > 0) {
         bin_count_kernel<<<(in->n + 255) / 256, 256, 0, st>>>(in->cell, in->n, n_cells, counts, ctx->stats);
+        note_launches(1);
+    }
     scan_local_kernel<<<nb, 256, 0, st>>>(counts, n_cells, slack_abs, slack_rel, incl, bsum);
     scan_blocks_kernel<<<1, 32, 0, st>>>(bsum, nb);
     scan_finish_kernel<<<(n_cells + 255) / 256, 256, 0, st>>>(incl, bsum, counts, n_cells, out->cell_start,
                                                              out->cell_count, out->cell_added, tm);
+    note_launches(3);
     long long h_tm[2] = {0, 0};
     e = cudaMemcpyAsync(h_tm, tm, sizeof(h_tm), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -313,6 +316,7 @@ extern "C" int pcc_bin(pcc_ctx* ctx, const pcc_particles* in, int n_cells, pcc_s
         Rec rt{tmp.ux, tmp.uy, tmp.uz, tmp.w, tmp.x, tmp.pid};
         MRec ro{out->ux, out->uy, out->uz, out->w, out->x, out->pid};
         cell_sort_kernel<<<n_cells, 256, smem, st>>>(out->cell_start, out->cell_count, m, rt, ro);
+        note_launches(2);
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? PCC_OK : cuda_fail(e, "pcc_bin: kernels");
@@ -327,6 +331,7 @@ extern "C" int pcc_append_secondaries(pcc_ctx* ctx, int n_cells, pcc_species* sp
     MRec r{sp->ux, sp->uy, sp->uz, sp->w, sp->x, sp->pid};
     commit_kernel<<<(n_cells + 255) / 256, 256, 0, (cudaStream_t)stream>>>(r, sp->cell_start, sp->cell_count,
                                                                             sp->cell_added, n_cells);
+    note_launches(1);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PCC_OK : cuda_fail(e, "pcc_append_secondaries");
 }
@@ -342,6 +347,7 @@ extern "C" int pcc_totals(pcc_ctx* ctx, int n_cells, const pcc_species* sp, int 
     cudaStream_t st = (cudaStream_t)stream;
     totals_kernel<<<blocks, 256, 0, st>>>(*sp, n_cells, is_photon, partial);
     totals_final_kernel<<<1, 32, 0, st>>>(partial, blocks, out);
+    note_launches(2);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PCC_OK : cuda_fail(e, "pcc_totals");
 }

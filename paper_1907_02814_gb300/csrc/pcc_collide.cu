@@ -1098,16 +1098,15 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
             }
             float spt = 0.f;
             const float inv_nt = 1.0f / (float)Nt;
-            for (uint32_t s = lane; s < Np; s += 32) {
-                const float wp = P.w[p0 + s];
-                if (caseA) {
+            if (caseA) {
+                for (uint32_t s = lane; s < Np; s += 32) {
                     const uint32_t j = NL <= 32 ? (uint32_t)tab[32 + s] : perm_pos_large(s, Np, rk);
-                    spt += fminf(wp, I.w[t0 + fast_mod(j, Nt, inv_nt)]);
-                } else {
-                    for (uint32_t j = s; j < Nt; j += Np) {
-                        const uint32_t t = NL <= 32 ? (uint32_t)tab[j] : perm_elem_large(j, Nt, rk);
-                        spt += fminf(wp, I.w[t0 + t]);
-                    }
+                    spt += fminf(P.w[p0 + s], I.w[t0 + fast_mod(j, Nt, inv_nt)]);
+                }
+            } else {   // lanes over the pairs: projectile j mod N_p, target P(j)
+                for (uint32_t j = lane; j < Nt; j += 32) {
+                    const uint32_t t = NL <= 32 ? (uint32_t)tab[j] : perm_elem_large(j, Nt, rk);
+                    spt += fminf(P.w[p0 + j % Np], I.w[t0 + t]);
                 }
             }
             n_pt = warp_sum(spt);
@@ -1143,21 +1142,24 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
                 }
             }
         } else {
+            // Draw units (pass m, slot pair q): unit i = m Qn + q covers slots 2q and
+            // 2q+1 of pass m, i.e. pairs j = s + m N_p.  Lanes take consecutive
+            // units, so each projectile's pairs are queued in increasing j.
             uint32_t cnt = 0;
-            for (uint32_t q0 = 0; 2 * q0 < Np; q0 += 32) {
-                const uint32_t q = q0 + lane;
-                const uint32_t passes = (Nt + Np - 1) / Np;
-                for (uint32_t mp = 0; mp < passes; ++mp) {
-                    const Philox4 ph = draw_k(q, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
+            const uint32_t Qn = (Np + 1) >> 1, passes = (Nt + Np - 1) / Np, units = Qn * passes;
+            for (uint32_t i0 = 0; i0 < units; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                const bool valid = i < units;
+                const uint32_t mp = valid ? i / Qn : 0u, q = valid ? i - mp * Qn : 0u;
+                const Philox4 ph = draw_k(q, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint32_t s = 2 * q + h, j = s + mp * Np;
-                        const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
-                        const bool cand = s < Np && j < Nt && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
-                        const unsigned m = __ballot_sync(0xffffffffu, cand);
-                        if (cand) Q.qb[t0 + cnt + __popc(m & ((1u << lane) - 1u))] = j;
-                        cnt += __popc(m);
-                    }
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t s = 2 * q + h, j = s + mp * Np;
+                    const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
+                    const bool cand = valid && s < Np && j < Nt && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
+                    const unsigned m = __ballot_sync(0xffffffffu, cand);
+                    if (cand) Q.qb[t0 + cnt + __popc(m & ((1u << lane) - 1u))] = j;
+                    cnt += __popc(m);
                 }
             }
             if (lane == 0) {
@@ -1483,8 +1485,14 @@ static StepArgs make_args(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em,
 static int persistent_grid(pcc_ctx* ctx, const void* fn, int smem, int want_per_sm)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchedThreads, smem) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+    for (const auto& o : ctx->occ)
+        if (o.fn == fn && o.smem == smem) per_sm = o.per_sm;
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchedThreads, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        ctx->occ.push_back({fn, smem, per_sm});
+    }
     if (want_per_sm > 0 && want_per_sm < per_sm) per_sm = want_per_sm;
     return per_sm * std::max(ctx->num_sms, 1);
 }
@@ -1590,7 +1598,51 @@ static cudaError_t launch_batched(pcc_ctx* ctx, const StepArgs& a, const Species
     const int gb = persistent_grid(ctx, (const void*)caseb_cand_kernel<GROUP>, stage, 0);
     caseb_cand_kernel<GROUP><<<gb, kBatchedThreads, stage, st>>>(a, Q, stage);
     finalize_kernel<GROUP><<<2 * std::max(ctx->num_sms, 1), 256, 0, st>>>(a, Q);
+    note_launches(6);
     return cudaSuccess;
+}
+
+static int table_stage_bytes(const pcc_ctx* ctx)
+{
+    const size_t tab_bytes = (size_t)ctx->n_mat * ctx->spec.n_rows * sizeof(float);
+    return (tab_bytes % 16 == 0 && tab_bytes <= 48 * 1024) ? (int)tab_bytes : 0;
+}
+
+template <int GROUP>
+static void warm_occupancy(pcc_ctx* ctx, int stage)
+{
+    if (ctx->minb == 2) persistent_grid(ctx, (const void*)scan_kernel<GROUP, 2>, 0, 0);
+    else if (ctx->minb == 3) persistent_grid(ctx, (const void*)scan_kernel<GROUP, 3>, 0, 0);
+    else persistent_grid(ctx, (const void*)scan_kernel<GROUP, 4>, 0, 0);
+    persistent_grid(ctx, (const void*)flat_cand_kernel<GROUP>, stage, 0);
+    persistent_grid(ctx, (const void*)caseb_cand_kernel<GROUP>, stage, 0);
+}
+
+int collide_prepare(pcc_ctx* ctx, const pcc_cells* cells, const pcc_species* em, const pcc_species* ep,
+                    const pcc_species* ph, const pcc_species* ion, unsigned mask, int precision)
+{
+    if (!ctx || !cells || !em || !ep || !ph || !ion || cells->n_cells < 1) {
+        set_error("pcc_collide: invalid argument");
+        return PCC_E_INVALID;
+    }
+    if (precision != PCC_FP32_BATCHED) return PCC_OK;
+    const unsigned groups = (mask & 0x700u) ? (mask & 0x700u) : 0x700u;
+    const bool ei = (mask & (PCC_BREMS | PCC_TRIDENT)) != 0, bh = (mask & PCC_BH) != 0;
+    const bool run_em = ei && (groups & PCC_GROUP_EM), run_ep = ei && (groups & PCC_GROUP_EP);
+    const bool run_ph = bh && (groups & PCC_GROUP_PH);
+    int rc = ensure_lists(ctx, cells->n_cells);
+    if (rc) return rc;
+    size_t cap_a = 0;
+    if (run_em) cap_a = std::max(cap_a, (size_t)em->capacity);
+    if (run_ep) cap_a = std::max(cap_a, (size_t)ep->capacity);
+    if (run_ph) cap_a = std::max(cap_a, (size_t)ph->capacity);
+    rc = ensure_queue(ctx, std::max<size_t>(cap_a, 1), std::max<size_t>((size_t)ion->capacity, 1));
+    if (rc) return rc;
+    const int stage = table_stage_bytes(ctx);
+    if (run_em) warm_occupancy<kGroupEm>(ctx, stage);
+    if (run_ep) warm_occupancy<kGroupEp>(ctx, stage);
+    if (run_ph) warm_occupancy<kGroupPh>(ctx, stage);
+    return PCC_OK;
 }
 
 extern "C" int pcc_set_schedule(pcc_ctx* ctx, int min_blocks_per_sm, int blocks_per_sm)
@@ -1636,20 +1688,14 @@ extern "C" int pcc_collide(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em
         if (run_em) collide_plain_kernel<kGroupEm><<<cells->n_cells, 128, 0, st>>>(a);
         if (run_ep) collide_plain_kernel<kGroupEp><<<cells->n_cells, 128, 0, st>>>(a);
         if (run_ph) collide_plain_kernel<kGroupPh><<<cells->n_cells, 128, 0, st>>>(a);
+        note_launches((unsigned)run_em + (unsigned)run_ep + (unsigned)run_ph);
     } else {
-        int rc = ensure_lists(ctx, cells->n_cells);
-        if (rc) return rc;
-        size_t cap_a = 0;
-        if (run_em) cap_a = std::max(cap_a, (size_t)em->capacity);
-        if (run_ep) cap_a = std::max(cap_a, (size_t)ep->capacity);
-        if (run_ph) cap_a = std::max(cap_a, (size_t)ph->capacity);
-        rc = ensure_queue(ctx, std::max<size_t>(cap_a, 1), std::max<size_t>((size_t)ion->capacity, 1));
+        int rc = collide_prepare(ctx, cells, em, ep, ph, ion, mask, precision);
         if (rc) return rc;
         // zero the class histograms and cursors of the three groups (see list_of)
         cudaError_t e = cudaMemsetAsync(ctx->lists + 10 * (size_t)ctx->lists_cells, 0, 6 * kClasses * sizeof(int), st);
         if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: list counters");
-        const size_t tab_bytes = (size_t)ctx->n_mat * ctx->spec.n_rows * sizeof(float);
-        const int stage = (tab_bytes % 16 == 0 && tab_bytes <= 48 * 1024) ? (int)tab_bytes : 0;
+        const int stage = table_stage_bytes(ctx);
         if (run_em && e == cudaSuccess) e = launch_batched<kGroupEm>(ctx, a, a.em, stage, st);
         if (run_ep && e == cudaSuccess) e = launch_batched<kGroupEp>(ctx, a, a.ep, stage, st);
         if (run_ph && e == cudaSuccess) e = launch_batched<kGroupPh>(ctx, a, a.ph, stage, st);
@@ -1672,6 +1718,7 @@ extern "C" int pcc_pairing(pcc_ctx* ctx, int n_cells, const pcc_species* proj, c
     a.step = step;
     pairing_kernel<<<std::max(1, std::min((n_cells + 7) / 8, 65535)), 256, 0, (cudaStream_t)stream>>>(
         a, view_of(*proj), view_of(*targ), group, out_j, out_t);
+    note_launches(1);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PCC_OK : cuda_fail(e, "pcc_pairing");
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/pcc.h"
 #include "pcc_device.cuh"
@@ -44,6 +45,15 @@ struct pcc_ctx {
     size_t queue_b_cap = 0;
     int minb = 4;                  // register budget: minimum resident blocks per SM
     int blocks_per_sm = 0;         // persistent grid cap (0: as many as fit)
+    // resident blocks per SM of the persistent kernels, by (kernel, dynamic smem)
+    struct Occ { const void* fn; int smem; int per_sm; };
+    std::vector<Occ> occ;
+    // captured multi-step graph
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    std::vector<cudaEvent_t> graph_events;   // per step: 5 events (see pcc_steps_capture)
+    int graph_steps = 0;
+    unsigned long long graph_kernels = 0;    // kernel nodes per launch of the graph
 };
 
 namespace pcc {
@@ -51,6 +61,9 @@ namespace pcc {
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);
 int ensure_scratch(pcc_ctx* ctx, size_t bytes);
+// Count kernel launches enqueued by the library (read by pcc_launch_count).
+void note_launches(unsigned long long n);
+unsigned long long launches_so_far();
 
 // Table geometry passed to kernels by value.
 struct TableGeom {
@@ -64,3 +77,10 @@ struct TableGeom {
 TableGeom make_geom(const pcc_table_spec& s);
 
 }  // namespace pcc
+
+// Buffers and launch geometry of a pcc_collide call with these arguments,
+// set up ahead (allocations, occupancy queries) so the call itself can be
+// captured into a graph.
+int collide_prepare(pcc_ctx* ctx, const pcc_cells* cells, const pcc_species* em, const pcc_species* ep,
+                    const pcc_species* ph, const pcc_species* ion, unsigned mask, int precision);
+void pcc_free_graph(pcc_ctx* ctx);

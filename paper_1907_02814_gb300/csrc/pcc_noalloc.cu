@@ -120,6 +120,7 @@ extern "C" int pcc_totals_noalloc(int n_cells, const pcc_species* sp, int is_pho
     cudaStream_t st = (cudaStream_t)stream;
     totals_block_kernel<<<nb, 256, 0, st>>>(*sp, n_cells, is_photon, partial);
     totals_sum_kernel<<<1, 32, 0, st>>>(partial, nb, out);
+    pcc::note_launches(2);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PCC_OK : pcc::cuda_fail(e, "pcc_totals_noalloc: launch");
 }

@@ -304,6 +304,7 @@ extern "C" int pcc_tables_build(pcc_ctx* ctx, const pcc_material* mats, int n_ma
     z_to_float_kernel<<<(n_mats + 63) / 64, 64, 0, st>>>(ctx->screen, ctx->f_Z, n_mats);
     bounds_kernel<<<(n_mats + 63) / 64, 64, 0, st>>>(ctx->screen, ctx->brems_sigma, ctx->bh_sigma, g, n_mats,
                                                      ctx->f_bound);
+    note_launches(13);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(dmats);

@@ -51,6 +51,12 @@ class Cells(C.Structure):
     _fields_ = [("n_cells", C.c_int), ("material_of_cell", _vp), ("ion_mass", C.c_double)]
 
 
+class StepDesc(C.Structure):
+    _fields_ = [("cells", C.POINTER(Cells)), ("em", C.POINTER(Species)), ("ep", C.POINTER(Species)),
+                ("ph", C.POINTER(Species)), ("ion", C.POINTER(Species)), ("dt", C.c_double), ("seed", C.c_uint64),
+                ("mask", C.c_uint), ("precision", C.c_int), ("ledger", _vp)]
+
+
 class Stats(C.Structure):
     _fields_ = [("pairs", C.c_ulonglong * 3), ("accepted", C.c_ulonglong * 5), ("created", C.c_ulonglong * 5),
                 ("energy_change", C.c_double), ("charge_change", C.c_double), ("candidates", C.c_ulonglong * 3)]
@@ -75,6 +81,10 @@ EXPORTS = {
     "pcc_totals": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.c_int, _vp, _vp]),
     "pcc_totals_noalloc": (C.c_int, [C.c_int, C.POINTER(Species), C.c_int, _vp, _vp]),
     "pcc_read_status": (C.c_int, [_vp, C.POINTER(C.c_uint), C.POINTER(Stats), _vp]),
+    "pcc_steps_capture": (C.c_int, [_vp, C.POINTER(StepDesc), C.c_uint64, C.c_int, C.c_int, _vp]),
+    "pcc_steps_launch": (C.c_int, [_vp, _vp]),
+    "pcc_steps_timing": (C.c_int, [_vp, _fp]),
+    "pcc_launch_count": (C.c_ulonglong, []),
     "pcc_expected_emission_fwd": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "pcc_expected_emission_bwd": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp,
                                             _vp]),
@@ -138,6 +148,7 @@ class Context:
         self.device = device
         self.spec = None
         self.n_mat = 0
+        self.graph_steps = 0
 
     def close(self):
         if getattr(self, "h", None):
@@ -170,6 +181,28 @@ class Context:
 
     def set_schedule(self, min_blocks_per_sm=4, blocks_per_sm=0):
         _check(self.lib.pcc_set_schedule(self.h, int(min_blocks_per_sm), int(blocks_per_sm)), "pcc_set_schedule")
+
+    def steps_capture(self, n_cells, material_of_cell, ion_mass, em, ep, ph, ion, dt, seed, step0, n_steps,
+                      mask=BREMS | TRIDENT | BH, precision=FP32_BATCHED, ledger=None, timing=False, stream=None):
+        """Capture n_steps full steps (collide of each group, then the three
+        commits) into one CUDA graph held by the context."""
+        cells = Cells(int(n_cells), _ptr(material_of_cell), float(ion_mass))
+        sp = [x.cstruct() for x in (em, ep, ph, ion)]
+        # the structs must outlive the call only; the graph keeps the device pointers
+        d = StepDesc(C.pointer(cells), C.pointer(sp[0]), C.pointer(sp[1]), C.pointer(sp[2]), C.pointer(sp[3]),
+                     float(dt), C.c_uint64(int(seed)), int(mask), int(precision), _ptr(ledger))
+        _check(self.lib.pcc_steps_capture(self.h, C.byref(d), C.c_uint64(int(step0)), int(n_steps),
+                                          int(bool(timing)), _stream(stream)), "pcc_steps_capture")
+        self.graph_steps = int(n_steps)
+
+    def steps_launch(self, stream=None):
+        _check(self.lib.pcc_steps_launch(self.h, _stream(stream)), "pcc_steps_launch")
+
+    def steps_timing(self):
+        """[n_steps][4] milliseconds: e- group, e+ group, photon group, commits."""
+        out = np.zeros((self.graph_steps, 4), dtype=np.float32)
+        _check(self.lib.pcc_steps_timing(self.h, out.ctypes.data_as(_fp)), "pcc_steps_timing")
+        return out
 
     def read_status(self, stream=None):
         st = C.c_uint(0)
@@ -280,6 +313,11 @@ def totals(ctx: Context, n_cells, sp: DeviceSpecies, is_photon=False, stream=Non
     return out
 
 
+def launch_count() -> int:
+    """Kernels enqueued by the library so far in this process."""
+    return int(load().pcc_launch_count())
+
+
 def totals_noalloc(n_cells, sp: DeviceSpecies, out, is_photon=False, stream=None):
     """Allocation-free totals into the caller's device double[3] `out`."""
     s = sp.cstruct()
@@ -288,8 +326,16 @@ def totals_noalloc(n_cells, sp: DeviceSpecies, out, is_photon=False, stream=None
     return out
 
 
+def _f32_cuda(name, t):
+    import torch
+    if t.dtype != torch.float32 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    return t.contiguous()
+
+
 def expected_emission_fwd(ctx: Context, Z, params, gamma, w, n_quad=64, stream=None):
     import torch
+    params, gamma, w = _f32_cuda("params", params), _f32_cuda("gamma", gamma), _f32_cuda("w", w)
     n_cells, n_samples = gamma.shape
     out = torch.empty((n_cells, 3), dtype=torch.float32, device=gamma.device)
     _check(ctx.lib.pcc_expected_emission_fwd(ctx.h, n_cells, n_samples, int(Z), int(n_quad), _ptr(params),
@@ -300,9 +346,11 @@ def expected_emission_fwd(ctx: Context, Z, params, gamma, w, n_quad=64, stream=N
 
 def expected_emission_bwd(ctx: Context, Z, params, gamma, w, grad_out, n_quad=64, stream=None):
     import torch
+    params, gamma, w = _f32_cuda("params", params), _f32_cuda("gamma", gamma), _f32_cuda("w", w)
+    grad_out = _f32_cuda("grad_out", grad_out)
     n_cells, n_samples = gamma.shape
     g = torch.empty((n_cells, 5), dtype=torch.float32, device=gamma.device)
     _check(ctx.lib.pcc_expected_emission_bwd(ctx.h, n_cells, n_samples, int(Z), int(n_quad), _ptr(params),
-                                             _ptr(gamma), _ptr(w), _ptr(grad_out.contiguous()), _ptr(g),
+                                             _ptr(gamma), _ptr(w), _ptr(grad_out), _ptr(g),
                                              _stream(stream)), "pcc_expected_emission_bwd")
     return g
