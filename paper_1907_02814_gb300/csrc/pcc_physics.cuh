@@ -48,7 +48,7 @@ __device__ inline double lambert_w0_neg(double z)
 }
 
 // sum_{n>=2} n^-s, summed downward to n = 2000 plus the Euler-Maclaurin tail.
-__device__ inline double zeta_tail(double s)
+__host__ __device__ inline double zeta_tail(double s)
 {
     double acc = 0.0;
     for (int n = 2000; n >= 2; --n) acc += exp(-s * log((double)n));
@@ -57,7 +57,7 @@ __device__ inline double zeta_tail(double s)
 }
 
 // Coulomb correction: a^2 [1/(1+a^2) + sum_{n=0}^{3} (-a^2)^n (zeta(2n+3) - 1)].
-__device__ inline double coulomb_fc(int Z)
+__host__ __device__ inline double coulomb_fc(int Z)
 {
     const double a2 = (kAlpha * Z) * (kAlpha * Z);
     double s = 0.0, p = 1.0;

@@ -1,0 +1,161 @@
+"""The expected-emission operator and its adjoint kernel against the FP64
+oracle (forward values and FP64 gradients), against central differences of
+the FP32 forward, through torch.autograd, and on edge cases."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1907_02814_gb300 import workloads as W  # noqa: E402
+
+NAMES = ("n_i", "T_e", "Zstar", "s_TF", "s_D")
+
+
+@pytest.fixture(scope="module")
+def pcc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_02814_gb300 import build, pcc as p
+    build.build()
+    return p
+
+
+@pytest.fixture(scope="module")
+def ctx(pcc):
+    c = pcc.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def data():
+    """4096 cells x 512 samples (log-uniform 0.5-200 MeV), parameters drawn
+    across both branches of the Debye length."""
+    d = W.emission_params()
+    params = np.stack([d[k] for k in NAMES], axis=1).astype(np.float32)
+    return {"Z": d["Z"], "params": params, "gamma": d["gamma"].astype(np.float32), "w": d["w"].astype(np.float32)}
+
+
+def to_dev(a):
+    return torch.as_tensor(a, device="cuda")
+
+
+def oracle_material(orc, Z, p):
+    p = [float(v) for v in p]
+    return orc.material(Z, p[2], p[0], p[1], p[3], p[4])
+
+
+def away_from_kink(orc, Z, p, margin=0.02):
+    s = orc.screening(oracle_material(orc, Z, p))
+    return abs(s.lambdaD / s.ri - 1.0) > margin
+
+
+def test_forward_matches_oracle(pcc, ctx, orc, data):
+    """Full size (4096 x 512, 64 nodes): sampled cells against the FP64
+    oracle on the same float32 inputs.  FP32 nodes with the rearranged I2 are
+    good to ~2e-7; compensated sums keep the cell totals within 2e-5."""
+    out = pcc.expected_emission_fwd(ctx, data["Z"], to_dev(data["params"]), to_dev(data["gamma"]),
+                                    to_dev(data["w"])).cpu().numpy()
+    st, _ = ctx.read_status()
+    assert st == 0 and np.all(np.isfinite(out)) and np.all(out[:, 0] > 0)
+    rng = np.random.default_rng(0)
+    for c in rng.choice(len(out), 24, replace=False):
+        mat = oracle_material(orc, data["Z"], data["params"][c])
+        ref = orc.expected_emission(mat, data["gamma"][c].astype(np.float64), data["w"][c].astype(np.float64))
+        np.testing.assert_allclose(out[c], ref, rtol=2e-5, err_msg=f"cell {c}")
+
+
+def test_gradient_matches_oracle(pcc, ctx, orc, data):
+    """Adjoint kernel vs the oracle's FP64 gradient for a random grad_out.
+    Each component is compared on the scale of its relative sensitivity:
+    |theta_k (g_k - ref_k)| <= 1e-3 |f| + 1e-3 |theta_k ref_k|."""
+    rng = np.random.default_rng(1)
+    cells = [c for c in rng.permutation(len(data["params"]))
+             if away_from_kink(orc, data["Z"], data["params"][c])][:10]
+    p = data["params"][cells]
+    g = data["gamma"][cells]
+    w = data["w"][cells]
+    gout = rng.uniform(0.5, 1.5, (len(cells), 3)).astype(np.float32)
+    gp = pcc.expected_emission_bwd(ctx, data["Z"], to_dev(p), to_dev(g), to_dev(w), to_dev(gout)).cpu().numpy()
+    for i in range(len(cells)):
+        mat = oracle_material(orc, data["Z"], p[i])
+        gg, ww = g[i].astype(np.float64), w[i].astype(np.float64)
+        ref = orc.expected_emission_grad(mat, gg, ww, gout[i].astype(np.float64))
+        f = float(np.dot(gout[i], orc.expected_emission(mat, gg, ww)))
+        th = p[i].astype(np.float64)
+        err = np.abs(th * (gp[i] - ref))
+        assert np.all(err <= 1e-3 * abs(f) + 1e-3 * np.abs(th * ref)), (i, gp[i], ref, f)
+
+
+def test_gradient_matches_fd_of_fp32_forward(pcc, ctx, orc, data):
+    """Adjoint vs central differences (h = 1e-3 relative) of the GPU forward
+    itself; the FP32 forward's ~1e-6 noise over 2h bounds the comparison
+    at ~1e-2 of |f| per unit relative step."""
+    rng = np.random.default_rng(2)
+    cells = [c for c in rng.permutation(len(data["params"]))
+             if away_from_kink(orc, data["Z"], data["params"][c], 0.05)][:16]
+    p = data["params"][cells].copy()
+    g, w = to_dev(data["gamma"][cells]), to_dev(data["w"][cells])
+    gout = rng.uniform(0.5, 1.5, (len(cells), 3)).astype(np.float32)
+    gp = pcc.expected_emission_bwd(ctx, data["Z"], to_dev(p), g, w, to_dev(gout)).cpu().numpy()
+    f0 = (pcc.expected_emission_fwd(ctx, data["Z"], to_dev(p), g, w).cpu().numpy().astype(np.float64) * gout).sum(1)
+    for k in range(5):
+        h = 1e-3 * p[:, k].astype(np.float64)
+        lo, hi = p.copy(), p.copy()
+        lo[:, k] = (p[:, k] - h).astype(np.float32)
+        hi[:, k] = (p[:, k] + h).astype(np.float32)
+        dh = hi[:, k].astype(np.float64) - lo[:, k].astype(np.float64)
+        fl = (pcc.expected_emission_fwd(ctx, data["Z"], to_dev(lo), g, w).cpu().numpy().astype(np.float64) * gout).sum(1)
+        fh = (pcc.expected_emission_fwd(ctx, data["Z"], to_dev(hi), g, w).cpu().numpy().astype(np.float64) * gout).sum(1)
+        fd = (fh - fl) / dh
+        th = p[:, k].astype(np.float64)
+        assert np.all(np.abs(th * (gp[:, k] - fd)) <= 1e-2 * np.abs(f0) + 1e-2 * np.abs(th * fd)), (NAMES[k], gp[:, k], fd)
+
+
+def test_autograd_function(pcc, ctx, data):
+    from paper_1907_02814_gb300.emission import expected_emission
+    p = to_dev(data["params"][:64]).requires_grad_(True)
+    g, w = to_dev(data["gamma"][:64]), to_dev(data["w"][:64])
+    out = expected_emission(ctx, data["Z"], p, g, w)
+    gout = torch.rand_like(out)
+    (out * gout).sum().backward()
+    ref = pcc.expected_emission_bwd(ctx, data["Z"], p.detach(), g, w, gout)
+    assert torch.equal(p.grad, ref)
+    assert torch.equal(out.detach(), pcc.expected_emission_fwd(ctx, data["Z"], p.detach(), g, w))
+
+
+def test_edge_cases(pcc, ctx, orc, data):
+    """No samples gives zeros; samples at rest or of zero weight contribute
+    nothing; cells whose electrons are all non-relativistic (the FP64 branch)
+    match the oracle; invalid parameters give NaN and a status bit; bad sizes
+    are rejected."""
+    Z = data["Z"]
+    p = to_dev(data["params"][:4])
+    empty = torch.zeros((4, 0), dtype=torch.float32, device="cuda")
+    assert torch.count_nonzero(pcc.expected_emission_fwd(ctx, Z, p, empty, empty)) == 0
+    g = to_dev(data["gamma"][:4]).clone()
+    w = to_dev(data["w"][:4]).clone()
+    base = pcc.expected_emission_fwd(ctx, Z, p, g[:, :256], w[:, :256])
+    g2, w2 = g.clone(), w.clone()
+    g2[:, 256:] = 1.0
+    w2[:, 300:] = 0.0
+    np.testing.assert_allclose(pcc.expected_emission_fwd(ctx, Z, p, g2, w2).cpu().numpy(), base.cpu().numpy(),
+                               rtol=1e-6)
+    rng = np.random.default_rng(3)
+    gnr = (1.0 + rng.uniform(0.02, 0.99, (4, 128))).astype(np.float32)
+    wnr = np.ones((4, 128), np.float32)
+    out = pcc.expected_emission_fwd(ctx, Z, p, to_dev(gnr), to_dev(wnr)).cpu().numpy()
+    for c in range(4):
+        ref = orc.expected_emission(oracle_material(orc, Z, data["params"][c]), gnr[c].astype(np.float64),
+                                    wnr[c].astype(np.float64))
+        np.testing.assert_allclose(out[c], ref, rtol=2e-5)
+    bad = p.clone()
+    bad[1, 0] = -1.0
+    ctx.read_status()
+    out = pcc.expected_emission_fwd(ctx, Z, bad, g, w).cpu().numpy()
+    st, _ = ctx.read_status()
+    assert st & pcc.ST_NONFINITE and np.all(np.isnan(out[1])) and np.all(np.isfinite(out[[0, 2, 3]]))
+    with pytest.raises(pcc.PccError):
+        pcc.expected_emission_fwd(ctx, Z, p, g, w, n_quad=129)
