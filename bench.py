@@ -26,7 +26,17 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = "batched_cu_1048576cells_lognormal_median64_sigma1.5_cap8192_dt1fs"
+FULL_CELLS = 1 << 20
+
+
+def workload_name(cells):
+    return f"batched_cu_{cells}cells_lognormal_median64_sigma1.5_cap8192_dt1fs"
+
+
+def workload_counts(W, cells, seed):
+    """The batched Cu workload; fewer cells keep the same occupancy law and
+    the same ions per electron (3e7 ions per 2^20 cells)."""
+    return W.batched_cu(n_cells=cells, seed=seed, total_ions=int(round(30_000_000 * cells / FULL_CELLS)))
 METRIC = "collision pairs/s"
 UNIT = "pairs/s"
 FALLBACK_HBM = 6800.0
@@ -245,7 +255,7 @@ def run_gpu(args):
     build.build()
     pcc.load()
     ctx = pcc.Context(local)
-    counts = W.batched_cu(seed=3 + rank)
+    counts = workload_counts(W, args.cells, 3 + rank)
     n_cells = len(counts["e"])
     dev = setup(ctx, pcc, W, torch, counts, SLACK)
     mat_of_cell = torch.zeros(n_cells, dtype=torch.int32, device="cuda")
@@ -308,6 +318,9 @@ def run_gpu(args):
 
     # end-to-end through the C ABI with host buffers
     e2e = e2e_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, seed, prec)
+    plain = plain_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, seed, ledger,
+                          pairs_all / args.steps / world) if prec == pcc.FP32_BATCHED and args.plain_steps > 0 else None
+    emission = emission_measure(ctx, pcc, torch, W) if not args.no_emission else None
 
     peak, peak_kind = peaks()
     K = args.steps
@@ -329,7 +342,7 @@ def run_gpu(args):
         "steps": K, "warmup": args.warmup, "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == pcc.FP32_BATCHED else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": n_cells, "electrons": before["em"], "ions": before["ion"],
+        "config": {"workload": workload_name(n_cells), "cells": n_cells, "electrons": before["em"], "ions": before["ion"],
                    "photons": before["ph"], "positrons": before["ep"], "precision": args.precision,
                    "l2": "inputs larger than L2 (about 7 GB of particle records), no flush",
                    "timed": f"{K} steps in one CUDA graph", "schedule": schedule and list(schedule["schedule"]),
@@ -345,6 +358,8 @@ def run_gpu(args):
                           "ms_parts": {"ei": ei_ms, "ep": float(np.mean(parts[:, 1])),
                                        "ph": float(np.mean(parts[:, 2])), "commit": float(np.mean(parts[:, 3]))}},
         "e2e": e2e,
+        "plain_fp64": plain and dict(plain, speedup_of_batched=plain["ms_per_step"] / (ms_max / K)),
+        "expected_emission": emission,
         "gpu_launches": int(launches),
         "clocks": clk,
         "status": status,
@@ -356,6 +371,59 @@ def run_gpu(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def plain_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, seed, ledger, pairs_per_step):
+    """The plain per-cell FP64 path (one block per cell) on the same state:
+    eager steps timed with CUDA events; same kernels as the FP64 parity tests."""
+    stream = torch.cuda.current_stream()
+    ms = []
+    for s in range(args.plain_steps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pcc.collide(ctx, n_cells, mat_of_cell, ion_mass, dev["em"], dev["ep"], dev["ph"], dev["ion"], dt, seed,
+                    20_000 + s, precision=pcc.FP64_PLAIN, ledger=ledger)
+        for k in ("em", "ep", "ph"):
+            pcc.append_secondaries(ctx, n_cells, dev[k])
+        b.record(stream)
+        torch.cuda.synchronize()
+        if s > 0:                       # the first step warms the plain kernels
+            ms.append(a.elapsed_time(b))
+    status, st = ctx.read_status()
+    m = float(np.mean(ms))
+    return {"ms_per_step": m, "value": pairs_per_step / (m * 1e-3), "unit": UNIT, "steps": len(ms),
+            "status": status}
+
+
+def emission_measure(ctx, pcc, torch, W, reps=5):
+    """Expected-emission operator at 4096 cells x 512 samples x 64 nodes:
+    forward and adjoint kernel times (CUDA events, median of reps)."""
+    d = W.emission_params()
+    params = torch.as_tensor(np.stack([d[k] for k in ("n_i", "T_e", "Zstar", "s_TF", "s_D")], 1),
+                             dtype=torch.float32, device="cuda")
+    g = torch.as_tensor(d["gamma"], dtype=torch.float32, device="cuda")
+    w = torch.as_tensor(d["w"], dtype=torch.float32, device="cuda")
+    gout = torch.ones((g.shape[0], 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, fn in (("fwd", lambda: pcc.expected_emission_fwd(ctx, d["Z"], params, g, w)),
+                     ("bwd", lambda: pcc.expected_emission_bwd(ctx, d["Z"], params, g, w, gout))):
+        fn()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[f"ms_{name}"] = float(np.median(ms))
+    samples = g.numel()
+    res.update({"cells": g.shape[0], "samples": samples, "nodes": 64,
+                "fwd_samples_per_s": samples / (res["ms_fwd"] * 1e-3),
+                "bwd_samples_per_s": samples / (res["ms_bwd"] * 1e-3)})
+    ctx.read_status()
+    return res
 
 
 def e2e_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, seed, prec):
@@ -432,7 +500,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_1907_02814_gb300 import workloads as W
-    counts = W.batched_cu(seed=3)
+    counts = workload_counts(W, args.cells, 3)
     per_step = []
     for s in range(args.warmup + args.steps):
         v, sample, _ = oracle_sample(counts, budget_s=args.cpu_budget / max(1, args.steps + args.warmup), seed=11 + s)
@@ -442,7 +510,7 @@ def run_reference(args):
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 oracle"},
+        "data": "synthetic", "config": {"workload": workload_name(args.cells), "precision": "fp64 oracle"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -458,6 +526,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--cells", type=int, default=FULL_CELLS, help="smaller cases keep the occupancy law")
+    ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 path (0: skip)")
+    ap.add_argument("--no-emission", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
