@@ -346,6 +346,7 @@ def run_gpu(args):
                    "photons": before["ph"], "positrons": before["ep"], "precision": args.precision,
                    "l2": "inputs larger than L2 (about 7 GB of particle records), no flush",
                    "timed": f"{K} steps in one CUDA graph", "schedule": schedule and list(schedule["schedule"]),
+                   "schedule_ms": schedule and schedule["ms"],
                    "parallelism": f"replicas{world}"},
         "events_per_s": events_all / (ms_max * 1e-3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -195,7 +195,7 @@ int pcc_collide(pcc_ctx *ctx, const pcc_cells *cells, pcc_species *em, pcc_speci
 /* Launch schedule of the batched FP32 collision kernels (no counterpart in
  * the paper; a performance setting that never changes results).  Cells are
  * processed one per warp, largest size class first; min_blocks_per_sm
- * (2, 3 or 4) selects the register budget of the kernel (a minimum of that
+ * (2 to 6) selects the register budget of the kernel (a minimum of that
  * many resident 256-thread blocks per SM) and blocks_per_sm caps the
  * persistent grid (0 = as many as fit).  Applies to later pcc_collide calls
  * on this context.  PCC_E_INVALID outside these ranges. */

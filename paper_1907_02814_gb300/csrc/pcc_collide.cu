@@ -1034,6 +1034,7 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
     int* tab = scratch[wid];
     uint2* wb = buf[wid];
     int nb = 0;   // staged candidates of this warp (warp-uniform)
+    unsigned long long npairs = 0, ncands = 0;   // lane 0's counts
     int n = 0;
     for (int k = 0; k < kClasses; ++k) n += L.hist[k];
     const int nwarps = gridDim.x * (blockDim.x >> 5);
@@ -1170,8 +1171,8 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
         }
         if (lane == 0) {
             Q.coef[cell] = coef;
-            atomicAdd(&bacc.pairs[GROUP], (unsigned long long)(caseA ? Np : Nt));
-            if (ncand) atomicAdd(&bacc.candidates[GROUP], (unsigned long long)ncand);
+            npairs += caseA ? Np : Nt;
+            ncands += ncand;
             if ((caseA ? Np : Nt) > 65536u || (uint32_t)cell > 0xFFFFFFu || a.step > 0x7FFFFull)
                 atomicOr(&bacc.status, PCC_ST_ID_RANGE);
         }
@@ -1184,6 +1185,10 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
         for (int i = lane; i < nb; i += 32)
             if ((uint32_t)(base_q + i) < Q.cap_flat) Q.flat[base_q + i] = wb[i];
         if (lane == 0 && (uint32_t)(base_q + nb) > Q.cap_flat) atomicOr(&bacc.status, PCC_ST_CAPACITY);
+    }
+    if (lane == 0) {
+        if (npairs) atomicAdd(&bacc.pairs[GROUP], npairs);
+        if (ncands) atomicAdd(&bacc.candidates[GROUP], ncands);
     }
     __syncthreads();
     block_acc_flush(bacc, a.st);
@@ -1590,9 +1595,13 @@ static cudaError_t launch_batched(pcc_ctx* ctx, const StepArgs& a, const Species
     const int blocks = (a.n_cells + 255) / 256;
     class_hist_kernel<<<blocks, 256, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
     class_scatter_kernel<<<blocks, 256, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
-    if (ctx->minb == 2) launch_scan<GROUP, 2>(ctx, a, L, Q, st);
-    else if (ctx->minb == 3) launch_scan<GROUP, 3>(ctx, a, L, Q, st);
-    else launch_scan<GROUP, 4>(ctx, a, L, Q, st);
+    switch (ctx->minb) {
+    case 2: launch_scan<GROUP, 2>(ctx, a, L, Q, st); break;
+    case 3: launch_scan<GROUP, 3>(ctx, a, L, Q, st); break;
+    case 5: launch_scan<GROUP, 5>(ctx, a, L, Q, st); break;
+    case 6: launch_scan<GROUP, 6>(ctx, a, L, Q, st); break;
+    default: launch_scan<GROUP, 4>(ctx, a, L, Q, st); break;
+    }
     const int gf = persistent_grid(ctx, (const void*)flat_cand_kernel<GROUP>, stage, 0);
     flat_cand_kernel<GROUP><<<gf, kBatchedThreads, stage, st>>>(a, Q, stage);
     const int gb = persistent_grid(ctx, (const void*)caseb_cand_kernel<GROUP>, stage, 0);
@@ -1611,9 +1620,13 @@ static int table_stage_bytes(const pcc_ctx* ctx)
 template <int GROUP>
 static void warm_occupancy(pcc_ctx* ctx, int stage)
 {
-    if (ctx->minb == 2) persistent_grid(ctx, (const void*)scan_kernel<GROUP, 2>, 0, 0);
-    else if (ctx->minb == 3) persistent_grid(ctx, (const void*)scan_kernel<GROUP, 3>, 0, 0);
-    else persistent_grid(ctx, (const void*)scan_kernel<GROUP, 4>, 0, 0);
+    switch (ctx->minb) {
+    case 2: persistent_grid(ctx, (const void*)scan_kernel<GROUP, 2>, 0, 0); break;
+    case 3: persistent_grid(ctx, (const void*)scan_kernel<GROUP, 3>, 0, 0); break;
+    case 5: persistent_grid(ctx, (const void*)scan_kernel<GROUP, 5>, 0, 0); break;
+    case 6: persistent_grid(ctx, (const void*)scan_kernel<GROUP, 6>, 0, 0); break;
+    default: persistent_grid(ctx, (const void*)scan_kernel<GROUP, 4>, 0, 0); break;
+    }
     persistent_grid(ctx, (const void*)flat_cand_kernel<GROUP>, stage, 0);
     persistent_grid(ctx, (const void*)caseb_cand_kernel<GROUP>, stage, 0);
 }
@@ -1647,7 +1660,7 @@ int collide_prepare(pcc_ctx* ctx, const pcc_cells* cells, const pcc_species* em,
 
 extern "C" int pcc_set_schedule(pcc_ctx* ctx, int min_blocks_per_sm, int blocks_per_sm)
 {
-    if (!ctx || min_blocks_per_sm < 2 || min_blocks_per_sm > 4 || blocks_per_sm < 0) {
+    if (!ctx || min_blocks_per_sm < 2 || min_blocks_per_sm > 6 || blocks_per_sm < 0) {
         set_error("pcc_set_schedule: invalid schedule");
         return PCC_E_INVALID;
     }

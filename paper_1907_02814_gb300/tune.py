@@ -3,9 +3,9 @@
 The speed of the batched electron-ion step depends on two choices that the
 best value of shifts with the occupancy distribution of the cells:
 
-  * the register budget of the scan kernel, compiled for a minimum of 2, 3
-    or 4 resident blocks per SM (more registers per thread against more
-    warps to hide memory latency);
+  * the register budget of the scan kernel, compiled for a minimum of 2 to
+    6 resident blocks per SM (more registers per thread against more warps
+    to hide memory latency);
   * the persistent grid, as blocks per SM (0 = as many as fit).
 
 ``tune`` times every candidate on a scratch copy of the caller's particle
@@ -19,7 +19,7 @@ from __future__ import annotations
 import json
 import os
 
-CANDIDATES = ((4, 0), (3, 0), (2, 0), (4, 3), (4, 2), (3, 2))
+CANDIDATES = ((4, 0), (5, 0), (6, 0), (3, 0), (2, 0), (4, 3), (5, 4))
 
 
 def default_cache_path() -> str:

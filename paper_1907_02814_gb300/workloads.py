@@ -327,3 +327,45 @@ def device_to_host(d):
     h["pid"] = h["pid"].view(np.uint64)
     h.pop("n", None)
     return h
+
+
+def precision_study(cells_per_material=12, mean_e=64, i_per_cell=32, seed=4, dt=20e-15, photon_frac=0.25):
+    """Precision-study inputs shaped like the Au foil, with the target
+    replaced by Ta (Z = 73, n_i = 5.55e28 m^-3) and Al (Z = 13, n_i =
+    6.0e28 m^-3), Z* in {0, Z/4, Z/2, 3Z/4, Z} and T_e in {10, 1e2, 1e3, 1e4}
+    eV (40 material states, ``cells_per_material`` cells each).  Electrons:
+    Poisson(mean_e) per cell, kinetic energy ~ E^-2 on 0.1-100 MeV,
+    isotropic, weights log-uniform over three decades; photons: Binomial(N_e,
+    photon_frac), k ~ k^-2 on [2, 200] m_e c^2; ions at rest, so that energy
+    and charge are conserved exactly by every event."""
+    rng = np.random.default_rng(seed)
+    mats = []
+    for Z, n_i in ((73, 5.55e28), (13, 6.0e28)):
+        for zf in (0.0, 0.25, 0.5, 0.75, 1.0):
+            for T_e in (10.0, 1e2, 1e3, 1e4):
+                mats.append(Material(Z, zf * Z, n_i, T_e))
+    n_cells = cells_per_material * len(mats)
+    mat_of_cell = np.repeat(np.arange(len(mats), dtype=np.int32), cells_per_material)
+    ne = rng.poisson(mean_e, n_cells)
+    cell_e = np.repeat(np.arange(n_cells), ne)
+    n = len(cell_e)
+    a, b = 0.1 / MEC2_MEV, 100.0 / MEC2_MEV
+    T = 1.0 / (1.0 / a - rng.uniform(0.0, 1.0, n) * (1.0 / a - 1.0 / b))
+    ux, uy, uz = _lepton_from_T(rng, T)
+    wmean = 3e25 / mean_e
+    w = wmean / (999.0 / (3.0 * np.log(10.0))) * 10.0 ** (3.0 * rng.uniform(0.0, 1.0, n))
+    em = _species(ux, uy, uz, w, cell_e)
+    ng = rng.binomial(ne, photon_frac)
+    cell_g = np.repeat(np.arange(n_cells), ng)
+    u = rng.uniform(0.0, 1.0, len(cell_g))
+    k = 1.0 / (1.0 / 2.0 - u * (1.0 / 2.0 - 1.0 / 200.0))
+    gx, gy, gz = _isotropic(rng, len(cell_g))
+    ph = _species(k * gx, k * gy, k * gz, np.full(len(cell_g), wmean), cell_g)
+    cell_i = np.repeat(np.arange(n_cells), i_per_cell)
+    n_i_cell = np.array([mats[m].n_i for m in mat_of_cell])
+    z = np.zeros(len(cell_i))
+    ion = _species(z, z, z, (n_i_cell / i_per_cell)[cell_i], cell_i)
+    wl = Workload("precision_ta_al", n_cells, mats, mat_of_cell, MASS_TA, dt, seed, 1)
+    wl.species = {"em": _shuffle_species(rng, em), "ep": empty_species(), "ph": _shuffle_species(rng, ph),
+                  "ion": _shuffle_species(rng, ion)}
+    return wl
