@@ -1041,12 +1041,21 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
     const SpeciesView& P = GROUP == kGroupEm ? a.em : (GROUP == kGroupEp ? a.ep : a.ph);
     const SpeciesView& I = a.ion;
     const uint32_t step32 = (uint32_t)a.step;
+    // Two-stage prefetch: the metadata of the cell after next, and the first
+    // 32 weights of both lists of the next cell, load while a cell is scanned.
     int kk = blockIdx.x * (blockDim.x >> 5) + wid;
     CellMeta next = load_meta(a, P, kk < n ? L.list[kk] : -1);
+    float next_tw = (uint32_t)lane < next.Nt ? I.w[next.t0 + lane] : 0.f;
+    float next_pw = (uint32_t)lane < next.Np ? P.w[next.p0 + lane] : 0.f;
+    CellMeta next2 = load_meta(a, P, kk + nwarps < n ? L.list[kk + nwarps] : -1);
     while (kk < n) {
         const CellMeta cm = next;
+        const float tw0 = next_tw, pw0 = next_pw;   // weights of slots lane of this cell
         kk += nwarps;
-        next = load_meta(a, P, kk < n ? L.list[kk] : -1);   // prefetch
+        next = next2;
+        next_tw = (uint32_t)lane < next.Nt ? I.w[next.t0 + lane] : 0.f;
+        next_pw = (uint32_t)lane < next.Np ? P.w[next.p0 + lane] : 0.f;
+        next2 = load_meta(a, P, kk + nwarps < n ? L.list[kk + nwarps] : -1);
         const uint32_t Np = cm.Np, Nt = cm.Nt;
         const int cell = cm.cell, p0 = cm.p0, t0 = cm.t0, mat = cm.mat;
         if (Np == 0 || Nt == 0) continue;
@@ -1055,26 +1064,26 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
             continue;
         }
         const bool caseA = Np >= Nt;
-        // ---- sums
-        const float w0 = I.w[t0];
+        // ---- sums (the first 32 weights of each list were prefetched)
+        const float w0 = __shfl_sync(0xffffffffu, tw0, 0);
         float sp = 0.f, st = 0.f, sf = 0.f;
         bool uni = true;
 #pragma unroll 4
         for (uint32_t s = lane; s < Nt; s += 32) {
-            const float wt = I.w[t0 + s];
+            const float wt = s < 32u ? tw0 : I.w[t0 + s];
             st += wt;
             uni &= (wt == w0);
         }
         if (caseA) {
 #pragma unroll 4
             for (uint32_t s = lane; s < Np; s += 32) {
-                const float wp = P.w[p0 + s];
+                const float wp = s < 32u ? pw0 : P.w[p0 + s];
                 sp += wp;
                 sf += fminf(wp, w0);
             }
         } else {   // projectile s takes part in ceil((N_t - s) / N_p) pairs
             for (uint32_t s = lane; s < Np; s += 32) {
-                const float wp = P.w[p0 + s];
+                const float wp = s < 32u ? pw0 : P.w[p0 + s];
                 sp += wp;
                 sf += fminf(wp, w0) * (float)((Nt - s + Np - 1) / Np);
             }
