@@ -258,6 +258,13 @@ __device__ CellScreen cell_screen(const float* p, int Z)
     return c;
 }
 
+// Screening quantities of every cell, one thread per cell (FP64).
+__global__ void screen_kernel(const float* __restrict__ params, int n_cells, int Z, CellScreen* __restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n_cells) out[c] = cell_screen(params + 5 * (size_t)c, Z);
+}
+
 struct EmArgs {
     int n_cells, n_samples, Z, n_quad;
     double fC;          // Coulomb correction f_C(Z)
@@ -267,6 +274,7 @@ struct EmArgs {
     const float* grad_out;
     float* out;
     DevStats* st;
+    const CellScreen* screen;   // per-cell screening, computed by screen_kernel
     float lx[kMaxQuad]; // ln x at the nodes
     float hw[kMaxQuad]; // half-width times weight
 };
@@ -367,15 +375,12 @@ __device__ __forceinline__ void nr_sample(const EmArgs& a, double g, double bw, 
 constexpr int kSums = 11;
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kEmThreads) emission_kernel(const __grid_constant__ EmArgs a)
+__global__ void __launch_bounds__(kEmThreads, GRAD ? 2 : 3) emission_kernel(const __grid_constant__ EmArgs a)
 {
-    __shared__ CellScreen cs_s;
     __shared__ double part[kEmWarps][kSums];
     const int c = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) cs_s = cell_screen(a.params + 5 * (size_t)c, a.Z);
-    __syncthreads();
-    const CellScreen cs = cs_s;
+    const CellScreen cs = a.screen[c];
     if (!cs.ok) {
         if (threadIdx.x == 0) {
             raise_status(a.st, PCC_ST_NONFINITE);
@@ -387,22 +392,23 @@ __global__ void __launch_bounds__(kEmThreads) emission_kernel(const __grid_const
     }
     Acc acc;
     for (int i = 0; i < 3; ++i) acc.r_nr[i] = acc.p_nr[i] = 0.0;
-    double pair = 0.0;
+    Kahan pair;
     const float LR = (float)cs.LR;
     const float* gs = a.gamma + (size_t)c * a.n_samples;
     const float* ws = a.w + (size_t)c * a.n_samples;
     for (int s = wid; s < a.n_samples; s += kEmWarps) {
         const float g = gs[s], wt = ws[s];
         if (!(g > 1.0f) || !(wt != 0.0f)) continue;               // at rest or no weight: no emission
-        const double gd = g, beta = sqrt(1.0 - 1.0 / (gd * gd));
-        if (g <= 2.0f) nr_sample<GRAD>(a, gd, wt * beta, cs, lane, acc);
-        else rel_sample<GRAD>(a, g, (float)(wt * beta), LR, g > 100.0f ? (float)a.fC : 0.0f, lane, acc);
-        if (lane == 0) pair += wt * beta * sigma_trident<double>((double)a.Z, gd);
+        const float T = g - 1.0f;
+        const float bw = wt * (sqrtf(T * (T + 2.0f)) / g);    // w beta, FP32 (the FP64 units are scarce)
+        if (g <= 2.0f) nr_sample<GRAD>(a, (double)g, (double)bw, cs, lane, acc);
+        else rel_sample<GRAD>(a, g, bw, LR, g > 100.0f ? (float)a.fC : 0.0f, lane, acc);
+        if (lane == 0) pair.add(bw * sigma_trident<float>((float)a.Z, g));
     }
     double v[kSums];
     v[0] = (double)acc.r.s - acc.r.c;
     v[1] = (double)acc.p.s - acc.p.c;
-    v[2] = pair;
+    v[2] = (double)pair.s - pair.c;
     v[3] = (double)acc.r_LR.s - acc.r_LR.c;
     v[4] = (double)acc.p_LR.s - acc.p_LR.c;
     for (int i = 0; i < 3; ++i) { v[5 + i] = acc.r_nr[i]; v[8 + i] = acc.p_nr[i]; }
@@ -531,10 +537,15 @@ int launch(pcc_ctx* ctx, bool grad, int n_cells, int n_samples, int Z, int n_qua
         a.lx[q] = (float)(mid + half * gx[q]);
         a.hw[q] = (float)(half * gw[q]);
     }
+    const int rc = ensure_scratch(ctx, (size_t)n_cells * sizeof(CellScreen));
+    if (rc) return rc;
+    CellScreen* screen = static_cast<CellScreen*>(ctx->scratch);
+    a.screen = screen;
     cudaStream_t st = (cudaStream_t)stream;
+    screen_kernel<<<(n_cells + 127) / 128, 128, 0, st>>>(params, n_cells, Z, screen);
     if (grad) emission_kernel<true><<<n_cells, kEmThreads, 0, st>>>(a);
     else emission_kernel<false><<<n_cells, kEmThreads, 0, st>>>(a);
-    note_launches(1);
+    note_launches(2);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PCC_OK : cuda_fail(e, name);
 }
