@@ -141,3 +141,33 @@ def test_full_size_batched_fp32_on_sampled_cells(pcc, setup, orc):
     assert stats["pairs"][0] == int(np.maximum(ce, ci)[both].sum())
     bothg = (cg > 0) & (ci > 0)
     assert stats["pairs"][2] == int(np.maximum(cg, ci)[bothg].sum())
+
+
+def secondary_pids(sp):
+    """Identifiers of the live secondaries (marker bit 63 set) on the device."""
+    cnt = sp.cell_count.long()
+    start = sp.cell_start[:-1].long()
+    run0 = torch.cumsum(cnt, 0) - cnt
+    n = int(cnt.sum())
+    idx = torch.repeat_interleave(start, cnt) + (torch.arange(n, device=cnt.device) - torch.repeat_interleave(run0, cnt))
+    pid = sp.pid[idx]
+    return pid[pid < 0]
+
+
+def test_full_size_fp32_vs_fp64_decision_mismatch(pcc, setup):
+    """After the two tests above, both states have taken the same first step,
+    one on the plain FP64 path and one on the batched FP32 path: over all
+    ~2.3e8 pairs the events (identified by their secondaries' ids) differ in
+    a fraction below 1e-5 of the pairs."""
+    ctx, counts, states, sample = setup
+    ce, ci, cg = counts["e"], counts["i"], counts["g"]
+    pairs = int(np.maximum(ce, ci)[(ce > 0) & (ci > 0)].sum()) + int(np.maximum(cg, ci)[(cg > 0) & (ci > 0)].sum())
+    diff, total = 0, 0
+    for k in ("em", "ep", "ph"):
+        a, b = secondary_pids(states[0][k]), secondary_pids(states[1][k])
+        total += int(a.numel())
+        diff += int((~torch.isin(a, b)).sum()) + int((~torch.isin(b, a)).sum())
+    print(f"\n[full size] FP32 vs FP64 GPU: {diff} differing secondaries of {total}, {pairs} pairs "
+          f"({diff / pairs:.2e} per pair)")
+    assert total > 50_000
+    assert diff <= 1e-5 * pairs
