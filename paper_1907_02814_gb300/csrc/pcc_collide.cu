@@ -942,14 +942,33 @@ struct Queue {
     uint32_t* qb;         // [target capacity] pair indices of candidates in cells with N_p < N_t,
                           // written into the cell's target region in increasing pair order per projectile
     int* cand;            // [n_cells] such candidates of the cell
-    float* coef;          // [n_cells] (n_p n_t / n_pt) c dt
     int* caseb;           // [n_cells] cells with N_p < N_t and candidates
     int* caseb_count;     // [1]
     int* flagged;         // [n_cells] cells with an event in this call
     int* flagged_count;   // [1]
     int* flag;            // [n_cells] 1 once listed (cleared by the finalize kernel)
     float2* evacc;        // [n_cells] this call's ledger contributions (radiated energy, created weight)
+    int4* rec;            // [2 n_cells] per cell with candidates: {p0, t0, N_p, N_t}, {mat, coef bits, 0, 0}
 };
+
+// The scan leaves the cell data the candidate kernels need in one 32-byte
+// record (a single sector) instead of five metadata arrays and the
+// coefficient.
+struct CellRec {
+    int p0, t0;
+    uint32_t Np, Nt;
+    int mat;
+    float coef;
+};
+
+__device__ __forceinline__ CellRec load_rec(const Queue& Q, int cell)
+{
+    const int4 r0 = Q.rec[2 * (size_t)cell], r1 = Q.rec[2 * (size_t)cell + 1];
+    CellRec c;
+    c.p0 = r0.x; c.t0 = r0.y; c.Np = (uint32_t)r0.z; c.Nt = (uint32_t)r0.w;
+    c.mat = r1.x; c.coef = __int_as_float(r1.y);
+    return c;
+}
 
 __device__ __forceinline__ void flag_cell(const Queue& Q, int cell)
 {
@@ -1179,7 +1198,10 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
             ncand = cnt;
         }
         if (lane == 0) {
-            Q.coef[cell] = coef;
+            if (ncand) {
+                Q.rec[2 * (size_t)cell] = make_int4(cm.p0, t0, (int)Np, (int)Nt);
+                Q.rec[2 * (size_t)cell + 1] = make_int4(mat, __float_as_int(coef), 0, 0);
+            }
             npairs += caseA ? Np : Nt;
             ncands += ncand;
             if ((caseA ? Np : Nt) > 65536u || (uint32_t)cell > 0xFFFFFFu || a.step > 0x7FFFFull)
@@ -1251,9 +1273,9 @@ __global__ void __launch_bounds__(kBatchedThreads, 4) flat_cand_kernel(const __g
         const int cell = (int)e.x;
         const uint32_t s = e.y;
         if (cell < 0 || cell >= a.n_cells) continue;
-        const CellMeta cm = load_meta(a, P, cell);
+        const CellRec cm = load_rec(Q, cell);
         const uint32_t Np = cm.Np, Nt = cm.Nt;
-        const float coef = Q.coef[cell];
+        const float coef = cm.coef;
         const Philox4 kp = draw_k(0, (uint32_t)cell, step32, stream_tag(GROUP, kPerm, 0), a.keys);
         PermKeys rk;
         rk.k[0] = kp.v[0]; rk.k[1] = kp.v[1]; rk.k[2] = kp.v[2]; rk.k[3] = kp.v[3];
@@ -1312,10 +1334,10 @@ __global__ void __launch_bounds__(kBatchedThreads, 2) caseb_cand_kernel(const __
     for (int kk = blockIdx.x * (blockDim.x >> 5) + wid; kk < n; kk += nwarps) {
         const int cell = Q.caseb[kk];
         if (cell < 0 || cell >= a.n_cells) continue;
-        const CellMeta cm = load_meta(a, P, cell);
+        const CellRec cm = load_rec(Q, cell);
         const uint32_t Np = cm.Np, Nt = cm.Nt;
         const int cnt = Q.cand[cell];
-        const float coef = Q.coef[cell];
+        const float coef = cm.coef;
         const Philox4 kp = draw_k(0, (uint32_t)cell, step32, stream_tag(GROUP, kPerm, 0), a.keys);
         PermKeys rk;
         rk.k[0] = kp.v[0]; rk.k[1] = kp.v[1]; rk.k[2] = kp.v[2]; rk.k[3] = kp.v[3];
@@ -1513,18 +1535,22 @@ static int persistent_grid(pcc_ctx* ctx, const void* fn, int smem, int want_per_
 
 // Per-call cell state of the batched path, one int buffer of n = n_cells:
 //   [0, 3n) cell lists of the three groups   [3n) candidates (N_p < N_t cells)
-//   [4n) coefficients                        [5n) cells with N_p < N_t candidates
+//   [4n) unused                              [5n) cells with N_p < N_t candidates
 //   [6n) cells with events                   [7n) listed flags
-//   [8n, 10n) ledger contributions (float2)  [10n) class histograms and cursors,
+//   [8n, 10n) ledger contributions (float2)  [R, R + 8n) cell records (int4 pairs,
+//   R = 10n rounded up to 4 ints)           [R + 8n) class histograms and cursors,
 //   then three counters (flat queue, N_p < N_t cells, cells with events).
 // Flags and contributions start at zero and are cleared by the finalize kernel.
+static size_t rec_off(size_t n) { return (10 * n + 3) & ~(size_t)3; }
+static size_t hist_off(size_t n) { return rec_off(n) + 8 * n; }
+
 static int ensure_lists(pcc_ctx* ctx, int n_cells)
 {
     if (ctx->lists && ctx->lists_cells >= n_cells) return PCC_OK;
     if (ctx->lists) cudaFree(ctx->lists);
     ctx->lists = nullptr;
     ctx->lists_cells = 0;
-    const size_t bytes = ((size_t)10 * n_cells + 6 * kClasses + 8) * sizeof(int);
+    const size_t bytes = (hist_off(n_cells) + 6 * kClasses + 8) * sizeof(int);
     cudaError_t e = cudaMalloc(&ctx->lists, bytes);
     if (e == cudaSuccess) e = cudaMemset(ctx->lists, 0, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: cell lists");
@@ -1558,12 +1584,12 @@ static CellList list_of(pcc_ctx* ctx, int group)
     const size_t n = ctx->lists_cells;
     CellList L;
     L.list = ctx->lists + (size_t)group * n;
-    L.hist = ctx->lists + 10 * n + (size_t)(2 * group) * kClasses;
+    L.hist = ctx->lists + hist_off(n) + (size_t)(2 * group) * kClasses;
     L.cursor = L.hist + kClasses;
     return L;
 }
 
-static int* counters_of(pcc_ctx* ctx) { return ctx->lists + 10 * (size_t)ctx->lists_cells + 6 * kClasses; }
+static int* counters_of(pcc_ctx* ctx) { return ctx->lists + hist_off(ctx->lists_cells) + 6 * kClasses; }
 
 static Queue queue_of(pcc_ctx* ctx)
 {
@@ -1575,13 +1601,13 @@ static Queue queue_of(pcc_ctx* ctx)
     Q.flat_count = c;
     Q.qb = (uint32_t*)ctx->queue_b;
     Q.cand = ctx->lists + 3 * n;
-    Q.coef = reinterpret_cast<float*>(ctx->lists + 4 * n);
     Q.caseb = ctx->lists + 5 * n;
     Q.caseb_count = c + 1;
     Q.flagged = ctx->lists + 6 * n;
     Q.flagged_count = c + 2;
     Q.flag = ctx->lists + 7 * n;
     Q.evacc = reinterpret_cast<float2*>(ctx->lists + 8 * n);
+    Q.rec = reinterpret_cast<int4*>(ctx->lists + rec_off(n));
     return Q;
 }
 
@@ -1715,7 +1741,7 @@ extern "C" int pcc_collide(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em
         int rc = collide_prepare(ctx, cells, em, ep, ph, ion, mask, precision);
         if (rc) return rc;
         // zero the class histograms and cursors of the three groups (see list_of)
-        cudaError_t e = cudaMemsetAsync(ctx->lists + 10 * (size_t)ctx->lists_cells, 0, 6 * kClasses * sizeof(int), st);
+        cudaError_t e = cudaMemsetAsync(ctx->lists + hist_off(ctx->lists_cells), 0, 6 * kClasses * sizeof(int), st);
         if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: list counters");
         const int stage = table_stage_bytes(ctx);
         if (run_em && e == cudaSuccess) e = launch_batched<kGroupEm>(ctx, a, a.em, stage, st);
