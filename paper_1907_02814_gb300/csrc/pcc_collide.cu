@@ -777,9 +777,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 
 struct CellList {
     int* list;       // [n_cells], cells by decreasing size class
-    int* hist;       // [kClasses]
-    int* cursor;     // [kClasses]
+    int* hist;       // [kClasses] cells per class
+    int* cursor;     // [kClasses] (unused)
+    int* bh;         // [kClasses][nblk] per-block class counts, then their offsets
+    int nblk;        // blocks of kClassBlock cells
 };
+
+constexpr int kClassBlock = 1024;                 // cells per class-sort block
+constexpr int kClassSmemMax = 200 * 1024;         // offsets scanned in shared memory up to this size
 
 __device__ __forceinline__ int size_class(int np, int nt)
 {
@@ -788,6 +793,10 @@ __device__ __forceinline__ int size_class(int np, int nt)
     return b < kClasses ? b : kClasses - 1;
 }
 
+// Counting sort of the cells with both species by decreasing size class,
+// in three passes without global atomics: per-block class counts, their
+// exclusive scan (classes from the largest, blocks in order), and the
+// scatter with ranks from shared-memory counters.
 __global__ void class_hist_kernel(const int* __restrict__ cnt_p, const int* __restrict__ cnt_t, int n_cells,
                                   CellList L)
 {
@@ -800,33 +809,70 @@ __global__ void class_hist_kernel(const int* __restrict__ cnt_p, const int* __re
         if (np > 0 && nt > 0) atomicAdd(&h[size_class(np, nt)], 1);
     }
     __syncthreads();
-    if (threadIdx.x < kClasses && h[threadIdx.x]) atomicAdd(&L.hist[threadIdx.x], h[threadIdx.x]);
+    if (threadIdx.x < kClasses) L.bh[threadIdx.x * L.nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// One block: bh[k][b] -> offset of block b's cells of class k in the list;
+// hist[k] -> cells of class k.  The counts are staged in shared memory when
+// they fit (SMEM = true), else scanned in place in global memory.
+template <bool SMEM>
+__global__ void __launch_bounds__(1024) class_offsets_kernel(CellList L)
+{
+    extern __shared__ int sm[];
+    __shared__ int part[1024];
+    __shared__ int tot[kClasses];
+    const int n = kClasses * L.nblk;
+    if (threadIdx.x < kClasses) tot[threadIdx.x] = 0;
+    int* v = SMEM ? sm : L.bh;
+    if (SMEM)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = L.bh[i];
+    __syncthreads();
+    // scan order: classes from the largest, blocks in order; thread t takes
+    // a contiguous chunk of that order
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per, i1 = min(i0 + per, n);
+    int sum = 0;
+    for (int e = i0; e < i1; ++e) {
+        const int k = kClasses - 1 - e / L.nblk;
+        const int x = v[k * L.nblk + e % L.nblk];
+        sum += x;
+        if (x) atomicAdd(&tot[k], x);
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive scan of the thread sums
+        const int t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - sum;
+    for (int e = i0; e < i1; ++e) {
+        int& x = v[(kClasses - 1 - e / L.nblk) * L.nblk + e % L.nblk];
+        const int c = x;
+        x = run;
+        run += c;
+    }
+    __syncthreads();
+    if (SMEM)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) L.bh[i] = sm[i];
+    if (threadIdx.x < kClasses) L.hist[threadIdx.x] = tot[threadIdx.x];
 }
 
 __global__ void class_scatter_kernel(const int* __restrict__ cnt_p, const int* __restrict__ cnt_t, int n_cells,
                                      CellList L)
 {
-    __shared__ int off[kClasses];
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int k = kClasses - 1; k >= 0; --k) {
-            off[k] = acc;
-            acc += L.hist[k];
-        }
-    }
+    __shared__ int rank[kClasses];
+    if (threadIdx.x < kClasses) rank[threadIdx.x] = 0;
     __syncthreads();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int cls = -1;
     if (c < n_cells) {
         const int np = cnt_p[c], nt = cnt_t[c];
-        if (np > 0 && nt > 0) cls = size_class(np, nt);
+        if (np > 0 && nt > 0) {
+            const int cls = size_class(np, nt);
+            L.list[L.bh[cls * L.nblk + blockIdx.x] + atomicAdd(&rank[cls], 1)] = c;
+        }
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, cls);
-    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
-    int base = 0;
-    if (cls >= 0 && lane == leader) base = atomicAdd(&L.cursor[cls], __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    if (cls >= 0) L.list[off[cls] + base + __popc(peers & ((1u << lane) - 1u))] = c;
 }
 
 // Stage the ln sigma rows (n_mat x n_rows floats) in shared memory with one
@@ -1539,7 +1585,8 @@ static int persistent_grid(pcc_ctx* ctx, const void* fn, int smem, int want_per_
 //   [6n) cells with events                   [7n) listed flags
 //   [8n, 10n) ledger contributions (float2)  [R, R + 8n) cell records (int4 pairs,
 //   R = 10n rounded up to 4 ints)           [R + 8n) class histograms and cursors,
-//   then three counters (flat queue, N_p < N_t cells, cells with events).
+//   then three counters (flat queue, N_p < N_t cells, cells with events), then
+//   the per-block class counts of the group being sorted.
 // Flags and contributions start at zero and are cleared by the finalize kernel.
 static size_t rec_off(size_t n) { return (10 * n + 3) & ~(size_t)3; }
 static size_t hist_off(size_t n) { return rec_off(n) + 8 * n; }
@@ -1550,7 +1597,8 @@ static int ensure_lists(pcc_ctx* ctx, int n_cells)
     if (ctx->lists) cudaFree(ctx->lists);
     ctx->lists = nullptr;
     ctx->lists_cells = 0;
-    const size_t bytes = (hist_off(n_cells) + 6 * kClasses + 8) * sizeof(int);
+    const size_t nblk = ((size_t)n_cells + kClassBlock - 1) / kClassBlock;
+    const size_t bytes = (hist_off(n_cells) + 6 * kClasses + 8 + kClasses * nblk) * sizeof(int);
     cudaError_t e = cudaMalloc(&ctx->lists, bytes);
     if (e == cudaSuccess) e = cudaMemset(ctx->lists, 0, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: cell lists");
@@ -1586,6 +1634,8 @@ static CellList list_of(pcc_ctx* ctx, int group)
     L.list = ctx->lists + (size_t)group * n;
     L.hist = ctx->lists + hist_off(n) + (size_t)(2 * group) * kClasses;
     L.cursor = L.hist + kClasses;
+    L.nblk = (int)((n + kClassBlock - 1) / kClassBlock);
+    L.bh = ctx->lists + hist_off(n) + 6 * kClasses + 8;   // shared by the groups (used in turn)
     return L;
 }
 
@@ -1627,9 +1677,11 @@ static cudaError_t launch_batched(pcc_ctx* ctx, const StepArgs& a, const Species
     if (e != cudaSuccess) return e;
     const CellList L = list_of(ctx, GROUP);
     const Queue Q = queue_of(ctx);
-    const int blocks = (a.n_cells + 255) / 256;
-    class_hist_kernel<<<blocks, 256, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
-    class_scatter_kernel<<<blocks, 256, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
+    class_hist_kernel<<<L.nblk, kClassBlock, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
+    const size_t off_smem = (size_t)kClasses * L.nblk * sizeof(int);
+    if (off_smem <= (size_t)kClassSmemMax) class_offsets_kernel<true><<<1, 1024, off_smem, st>>>(L);
+    else class_offsets_kernel<false><<<1, 1024, 0, st>>>(L);
+    class_scatter_kernel<<<L.nblk, kClassBlock, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
     switch (ctx->minb) {
     case 2: launch_scan<GROUP, 2>(ctx, a, L, Q, st); break;
     case 3: launch_scan<GROUP, 3>(ctx, a, L, Q, st); break;
@@ -1642,7 +1694,7 @@ static cudaError_t launch_batched(pcc_ctx* ctx, const StepArgs& a, const Species
     const int gb = persistent_grid(ctx, (const void*)caseb_cand_kernel<GROUP>, stage, 0);
     caseb_cand_kernel<GROUP><<<gb, kBatchedThreads, stage, st>>>(a, Q, stage);
     finalize_kernel<GROUP><<<2 * std::max(ctx->num_sms, 1), 256, 0, st>>>(a, Q);
-    note_launches(6);
+    note_launches(7);
     return cudaSuccess;
 }
 
@@ -1669,6 +1721,12 @@ static void warm_occupancy(pcc_ctx* ctx, int stage)
 int collide_prepare(pcc_ctx* ctx, const pcc_cells* cells, const pcc_species* em, const pcc_species* ep,
                     const pcc_species* ph, const pcc_species* ion, unsigned mask, int precision)
 {
+    if (!ctx->class_smem_ready) {   // per device, before any capture
+        if (cudaFuncSetAttribute(class_offsets_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kClassSmemMax) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "pcc_collide: class sort shared memory");
+        ctx->class_smem_ready = true;
+    }
     if (!ctx || !cells || !em || !ep || !ph || !ion || cells->n_cells < 1) {
         set_error("pcc_collide: invalid argument");
         return PCC_E_INVALID;

@@ -45,6 +45,7 @@ struct pcc_ctx {
     size_t queue_b_cap = 0;
     int minb = 4;                  // register budget: minimum resident blocks per SM
     int blocks_per_sm = 0;         // persistent grid cap (0: as many as fit)
+    bool class_smem_ready = false; // large shared memory enabled for the class-sort offsets
     // resident blocks per SM of the persistent kernels, by (kernel, dynamic smem)
     struct Occ { const void* fn; int smem; int per_sm; };
     std::vector<Occ> occ;

@@ -101,7 +101,7 @@ def test_graph_matches_eager_steps(pcc, ctx, precision):
 
 
 def test_launch_count(pcc, ctx):
-    """The counter adds 6 kernels per batched group, 1 per plain group, 1
+    """The counter adds 7 kernels per batched group, 1 per plain group, 1
     per commit, and the kernel nodes of a graph per graph launch."""
     wl = workload(n_cells=16, seed=12)
     tables(pcc, ctx, wl)
@@ -110,7 +110,7 @@ def test_launch_count(pcc, ctx):
     c0 = pcc.launch_count()
     pcc.collide(ctx, wl.n_cells, mat, wl.ion_mass, d["em"], d["ep"], d["ph"], d["ion"], wl.dt, wl.seed, 0,
                 precision=pcc.FP32_BATCHED)
-    assert pcc.launch_count() - c0 == 18
+    assert pcc.launch_count() - c0 == 21
     c0 = pcc.launch_count()
     pcc.collide(ctx, wl.n_cells, mat, wl.ion_mass, d["em"], d["ep"], d["ph"], d["ion"], wl.dt, wl.seed, 1,
                 mask=pcc.BREMS | pcc.GROUP_EM, precision=pcc.FP64_PLAIN)
@@ -123,7 +123,7 @@ def test_launch_count(pcc, ctx):
     ctx.steps_launch()
     ctx.steps_launch()
     torch.cuda.synchronize()
-    assert pcc.launch_count() - c0 == 2 * 2 * (18 + 3)
+    assert pcc.launch_count() - c0 == 2 * 2 * (21 + 3)
     ctx.read_status()
 
 
