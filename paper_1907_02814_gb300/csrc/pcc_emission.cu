@@ -20,7 +20,8 @@
 // (the same function; g by its odd series for z < 1/4), and atan L - atan u
 // as atan(L(1-d)/(1+L u)).  Non-relativistic nodes (gamma <= 2, a small
 // share of samples, warp-uniform because a warp takes one sample) run in
-// FP64.  Sums over nodes and samples use compensated FP32 per lane and FP64
+// FP32 in a rearranged form (nr_sample32), or in FP64 in cells where L_D is
+// within 5 % of L_TF, where the cross term's divided difference cancels.  Sums over nodes and samples use compensated FP32 per lane and FP64
 // across lanes and warps.
 //
 // Adjoint.  The parameters enter only through the screening quantities
@@ -234,6 +235,7 @@ struct CellScreen {
     double LTF, LD, etaTF, etaD, a, LR;
     double n_i, T_e, Zs, sTF, sD;
     bool debye;   // lambda_D > r_i (the Debye branch of L_D is active)
+    bool nr32;    // L_D and L_TF far enough apart for the FP32 non-relativistic branch
     bool ok;
 };
 
@@ -255,6 +257,8 @@ __device__ CellScreen cell_screen(const float* p, int Z)
     c.a = i_tfd(c.etaTF, c.LTF, c.etaD, c.LD);
     const double w = lambert_w0_neg(-exp(-1.0 - 2.0 * c.a));
     c.LR = sqrt(expm1(w + 1.0 + 2.0 * c.a));
+    const double A = c.LTF * c.LTF, B = c.LD * c.LD;
+    c.nr32 = fabs(B - A) > 0.05 * fmax(A, B);
     return c;
 }
 
@@ -321,6 +325,72 @@ __device__ __forceinline__ void rel_sample(const EmArgs& a, float g, float bw, f
     acc.r.add(bw * sr);
     acc.p.add(bw * sp);
     if (GRAD) { acc.r_LR.add(bw * dr); acc.p_LR.add(bw * dp); }
+}
+
+// FP32 form of Eq. (cs_br_nr) with the Elwert factor, used when L_D and L_TF
+// differ by more than 5 %.  With P = q+^2 - q-^2 = 4 p1 p2 exactly, the
+// Yukawa terms are log1p(P L^2 / D-) - P L^2 / (D+ D-) and the cross term is
+// (B log1p(P A / T-) - A log1p(P B / D-)) / (B - A), A = L_TF^2, B = L_D^2:
+// no difference of nearly equal numbers is formed.
+template <typename R>
+__device__ __forceinline__ R nr_g32(float P, float qp, float qm, R eta, R L)
+{
+    const R L2 = L * L;
+    const R Dp = 1.0f + (qp * qp) * L2, Dm = 1.0f + (qm * qm) * L2;
+    return 0.5f * (eta * eta) * (f_log1p((P * L2) / Dm) - (P * L2) / (Dp * Dm));
+}
+
+template <typename R>
+__device__ __forceinline__ R nr_cross32(float P, float qm, R eTF, R LTF, R eD, R LD)
+{
+    const R A = LTF * LTF, B = LD * LD;
+    const R Tm = 1.0f + (qm * qm) * A, Dm = 1.0f + (qm * qm) * B;
+    return eTF * eD / (B - A) * (B * f_log1p((P * A) / Tm) - A * f_log1p((P * B) / Dm));
+}
+
+template <bool GRAD>
+__device__ __forceinline__ void nr_sample32(const EmArgs& a, float g, float bw, const CellScreen& cs, int lane,
+                                            Acc& acc)
+{
+    const float T1 = g - 1.0f, p1 = sqrtf(T1 * (T1 + 2.0f)), b1 = p1 / g;
+    const float az = 2.0f * (float)kPi * (float)a.Z * (float)kAlpha;
+    const float ex1 = -expm1f(-az / b1);
+    float sr = 0.f, sp = 0.f, dr[3] = {0.f, 0.f, 0.f}, dp[3] = {0.f, 0.f, 0.f};
+    for (int q = lane; q < a.n_quad; q += 32) {
+        const float l = a.lx[q];
+        const float x = expf(l), k = x * T1;
+        const float T2 = T1 * (-expm1f(l));
+        if (!(k > 0.f && T2 > 0.f)) continue;
+        const float p2 = sqrtf(T2 * (T2 + 2.0f));
+        const float qp = p1 + p2, qm = k * (T1 + T2 + 2.0f) / qp;
+        const float b2 = p2 / (1.0f + T2);
+        const float fE = (b1 / b2) * ex1 / (-expm1f(-az / b2));
+        const float pre = 4.0f / (3.0f * p1 * p1) * fE;
+        const float P = 4.0f * p1 * p2;
+        float fv, fd[3] = {0.f, 0.f, 0.f};
+        if (GRAD) {
+            Dual<float, 3> LTF = mk<float, 3>((float)cs.LTF), LD = mk<float, 3>((float)cs.LD);
+            Dual<float, 3> eD = mk<float, 3>((float)cs.etaD), eTF = mk<float, 3>((float)cs.etaTF);
+            LTF.d[0] = 1.0f; LD.d[1] = 1.0f; eD.d[2] = 1.0f; eTF.d[2] = -1.0f;
+            const Dual<float, 3> br = nr_g32(P, qp, qm, eTF, LTF) + nr_g32(P, qp, qm, eD, LD) +
+                                      nr_cross32(P, qm, eTF, LTF, eD, LD);
+            fv = pre * br.v;
+            for (int i = 0; i < 3; ++i) fd[i] = pre * br.d[i];
+        } else {
+            const float LTF = (float)cs.LTF, LD = (float)cs.LD, eTF = (float)cs.etaTF, eD = (float)cs.etaD;
+            fv = pre * (nr_g32(P, qp, qm, eTF, LTF) + nr_g32(P, qp, qm, eD, LD) + nr_cross32(P, qm, eTF, LTF, eD, LD));
+        }
+        if (!(fv > 0.f)) { fv = 0.f; fd[0] = fd[1] = fd[2] = 0.f; }
+        const float h = a.hw[q];
+        sr += h * fv;
+        sp += h * fv * k;
+        if (GRAD)
+            for (int i = 0; i < 3; ++i) { dr[i] += h * fd[i]; dp[i] += h * fd[i] * k; }
+    }
+    acc.r.add(bw * sr);
+    acc.p.add(bw * sp);
+    if (GRAD)
+        for (int i = 0; i < 3; ++i) { acc.r_nr[i] += (double)(bw * dr[i]); acc.p_nr[i] += (double)(bw * dp[i]); }
 }
 
 template <bool GRAD>
@@ -401,7 +471,10 @@ __global__ void __launch_bounds__(kEmThreads, GRAD ? 2 : 3) emission_kernel(cons
         if (!(g > 1.0f) || !(wt != 0.0f)) continue;               // at rest or no weight: no emission
         const float T = g - 1.0f;
         const float bw = wt * (sqrtf(T * (T + 2.0f)) / g);    // w beta, FP32 (the FP64 units are scarce)
-        if (g <= 2.0f) nr_sample<GRAD>(a, (double)g, (double)bw, cs, lane, acc);
+        if (g <= 2.0f) {
+            if (cs.nr32) nr_sample32<GRAD>(a, g, bw, cs, lane, acc);
+            else nr_sample<GRAD>(a, (double)g, (double)bw, cs, lane, acc);
+        }
         else rel_sample<GRAD>(a, g, bw, LR, g > 100.0f ? (float)a.fC : 0.0f, lane, acc);
         if (lane == 0) pair.add(bw * sigma_trident<float>((float)a.Z, g));
     }

@@ -128,9 +128,9 @@ def test_autograd_function(pcc, ctx, data):
 
 def test_edge_cases(pcc, ctx, orc, data):
     """No samples gives zeros; samples at rest or of zero weight contribute
-    nothing; cells whose electrons are all non-relativistic (the FP64 branch)
-    match the oracle; invalid parameters give NaN and a status bit; bad sizes
-    are rejected."""
+    nothing; cells whose electrons are all non-relativistic match the oracle,
+    on the FP32 branch and (L_D within 1 % of L_TF) on the FP64 branch;
+    invalid parameters give NaN and a status bit; bad sizes are rejected."""
     Z = data["Z"]
     p = to_dev(data["params"][:4])
     empty = torch.zeros((4, 0), dtype=torch.float32, device="cuda")
@@ -149,6 +149,18 @@ def test_edge_cases(pcc, ctx, orc, data):
     out = pcc.expected_emission_fwd(ctx, Z, p, to_dev(gnr), to_dev(wnr)).cpu().numpy()
     for c in range(4):
         ref = orc.expected_emission(oracle_material(orc, Z, data["params"][c]), gnr[c].astype(np.float64),
+                                    wnr[c].astype(np.float64))
+        np.testing.assert_allclose(out[c], ref, rtol=2e-5)
+    # cells with L_D within 1 % of L_TF take the FP64 non-relativistic branch
+    near = data["params"][:4].copy()
+    for c in range(4):
+        s0 = orc.screening(oracle_material(orc, Z, near[c]))
+        near[c, 4] = np.float32(near[c, 4] * 1.01 * s0.LTF / s0.LD)
+    out = pcc.expected_emission_fwd(ctx, Z, to_dev(near), to_dev(gnr), to_dev(wnr)).cpu().numpy()
+    for c in range(4):
+        s1 = orc.screening(oracle_material(orc, Z, near[c]))
+        assert abs(s1.LD / s1.LTF - 1.0) < 0.02
+        ref = orc.expected_emission(oracle_material(orc, Z, near[c]), gnr[c].astype(np.float64),
                                     wnr[c].astype(np.float64))
         np.testing.assert_allclose(out[c], ref, rtol=2e-5)
     bad = p.clone()
