@@ -1721,15 +1721,15 @@ static void warm_occupancy(pcc_ctx* ctx, int stage)
 int collide_prepare(pcc_ctx* ctx, const pcc_cells* cells, const pcc_species* em, const pcc_species* ep,
                     const pcc_species* ph, const pcc_species* ion, unsigned mask, int precision)
 {
+    if (!ctx || !cells || !em || !ep || !ph || !ion || cells->n_cells < 1) {
+        set_error("pcc_collide: invalid argument");
+        return PCC_E_INVALID;
+    }
     if (!ctx->class_smem_ready) {   // per device, before any capture
         if (cudaFuncSetAttribute(class_offsets_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kClassSmemMax) != cudaSuccess)
             return cuda_fail(cudaGetLastError(), "pcc_collide: class sort shared memory");
         ctx->class_smem_ready = true;
-    }
-    if (!ctx || !cells || !em || !ep || !ph || !ion || cells->n_cells < 1) {
-        set_error("pcc_collide: invalid argument");
-        return PCC_E_INVALID;
     }
     if (precision != PCC_FP32_BATCHED) return PCC_OK;
     const unsigned groups = (mask & 0x700u) ? (mask & 0x700u) : 0x700u;
