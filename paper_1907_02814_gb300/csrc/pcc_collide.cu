@@ -766,10 +766,11 @@ __global__ void __launch_bounds__(128) collide_plain_kernel(const __grid_constan
 }
 
 // Batched FP32 -----------------------------------------------------------------
-// Every cell with both lists non-empty is processed by one warp.  Cells are
-// listed by decreasing size class (bit length of N_pair) and dealt to the
-// warps of a persistent grid round-robin, so each warp receives a similar
-// share of large and small cells.
+// Every cell with both lists non-empty is scanned by one warp, or by a lane
+// group of one when it is small.  Cells are listed by decreasing size class
+// (bit length of N_pair) and dealt to the warps of a persistent grid
+// round-robin, so each warp receives a similar share of large and small
+// cells.
 constexpr int kBatchedThreads = 256;
 constexpr int kClasses = 18;
 
@@ -1079,13 +1080,256 @@ __device__ __forceinline__ bool bh_candidate(const StepArgs& a, const Tab<float>
 
 constexpr int kWarpBuf = 128;   // per-warp staging of candidates before the flat queue
 
-// Scan: for each cell (one warp), the sums n_p, n_t, n_pt of Sec. III.A, the
+// Sum over the G consecutive lanes of an aligned lane group (G a power of two).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v)
+{
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// n_pt of one cell summed over its actual pairs, for cells whose target
+// weights are not all equal.  All 32 lanes take part; the result is
+// warp-uniform.  Lists of at most 32 entries are permuted by rank keys
+// staged in tab (64 ints), longer ones by the Feistel walk.
+template <int GROUP>
+__device__ __forceinline__ float npt_over_pairs(const StepArgs& a, const SpeciesView& P, int cell, int p0, int t0,
+                                                uint32_t Np, uint32_t Nt, int* tab, int lane)
+{
+    const SpeciesView& I = a.ion;
+    const bool caseA = Np >= Nt;
+    const Philox4 kp = draw_k(0, (uint32_t)cell, (uint32_t)a.step, stream_tag(GROUP, kPerm, 0), a.keys);
+    PermKeys rk;
+    rk.k[0] = kp.v[0]; rk.k[1] = kp.v[1]; rk.k[2] = kp.v[2]; rk.k[3] = kp.v[3];
+    const uint32_t NL = caseA ? Np : Nt;
+    if (NL <= 32) {
+        __syncwarp();
+        if (lane < (int)NL) {
+            const uint32_t r = perm_pos_small(lane, NL, rk);
+            tab[r] = lane;    // P table
+            tab[32 + lane] = r;
+        }
+        __syncwarp();
+    }
+    float spt = 0.f;
+    const float inv_nt = 1.0f / (float)Nt;
+    if (caseA) {
+        for (uint32_t s = lane; s < Np; s += 32) {
+            const uint32_t j = NL <= 32 ? (uint32_t)tab[32 + s] : perm_pos_large(s, Np, rk);
+            spt += fminf(P.w[p0 + s], I.w[t0 + fast_mod(j, Nt, inv_nt)]);
+        }
+    } else {   // lanes over the pairs: projectile j mod N_p, target P(j)
+        for (uint32_t j = lane; j < Nt; j += 32) {
+            const uint32_t t = NL <= 32 ? (uint32_t)tab[j] : perm_elem_large(j, Nt, rk);
+            spt += fminf(P.w[p0 + j % Np], I.w[t0 + t]);
+        }
+    }
+    return warp_sum(spt);
+}
+
+// Scan state of one warp, carried from one size-class segment to the next.
+struct ScanWarp {
+    int nb;                              // candidates staged in the warp buffer (warp-uniform)
+    unsigned long long npairs, ncands;   // counts of the cells this lane leads
+};
+
+__device__ __forceinline__ void flush_staged(const Queue& Q, const uint2* wb, int nb, BlockAcc& bacc, int lane)
+{
+    __syncwarp();
+    int base_q = 0;
+    if (lane == 0) base_q = atomicAdd(Q.flat_count, nb);
+    base_q = __shfl_sync(0xffffffffu, base_q, 0);
+    for (int i = lane; i < nb; i += 32)
+        if ((uint32_t)(base_q + i) < Q.cap_flat) Q.flat[base_q + i] = wb[i];
+    if (lane == 0 && (uint32_t)(base_q + nb) > Q.cap_flat) atomicOr(&bacc.status, PCC_ST_CAPACITY);
+    __syncwarp();
+}
+
+// The cells of list entries [e0, e1), taken C = 32 / G at a time by a warp:
+// lane group g (lanes gG .. gG + G - 1) owns one cell, its lane l owns slots
+// base + 2l and base + 2l + 1 per pass, whose accept uniforms are the four
+// words of the lane's Philox draw (the counter depends on the slot, not on
+// the lane, so the random stream does not depend on G).  Tuples of C
+// entries are dealt to the warps round-robin starting at tuple t_first.
+// Loops that hold ballots run to the largest trip count of the warp's
+// groups, so every collective is reached by all 32 lanes.
+template <int GROUP, int G>
+__device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& L, const Queue& Q, int e0, int e1,
+                                             int t_first, int nwarps, int* tab, uint2* wb, ScanWarp& sw,
+                                             BlockAcc& bacc)
+{
+    constexpr int C = 32 / G;
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31, gi = lane / G, gl = lane % G;
+    const unsigned gmask = G == 32 ? kFull : ((1u << G) - 1u) << (gi * G);
+    const unsigned below = (1u << lane) - 1u;
+    const SpeciesView& P = GROUP == kGroupEm ? a.em : (GROUP == kGroupEp ? a.ep : a.ph);
+    const SpeciesView& I = a.ion;
+    const uint32_t step32 = (uint32_t)a.step;
+    const int ntup = (e1 - e0 + C - 1) / C;
+    const int e_lane = e0 + gi;   // entry of tuple t for this lane: e_lane + t C
+    // Two-stage prefetch: the metadata of the tuple after next, and the first
+    // G weights of both lists of the next tuple, load while a tuple is scanned.
+    int t = t_first;
+    CellMeta next = load_meta(a, P, t < ntup && e_lane + t * C < e1 ? L.list[e_lane + t * C] : -1);
+    float next_tw = (uint32_t)gl < next.Nt ? I.w[next.t0 + gl] : 0.f;
+    float next_pw = (uint32_t)gl < next.Np ? P.w[next.p0 + gl] : 0.f;
+    int t2 = t + nwarps;
+    CellMeta next2 = load_meta(a, P, t2 < ntup && e_lane + t2 * C < e1 ? L.list[e_lane + t2 * C] : -1);
+    while (t < ntup) {
+        const CellMeta cm = next;
+        const float tw0 = next_tw, pw0 = next_pw;   // weights of slot gl of this cell
+        t += nwarps;
+        next = next2;
+        next_tw = (uint32_t)gl < next.Nt ? I.w[next.t0 + gl] : 0.f;
+        next_pw = (uint32_t)gl < next.Np ? P.w[next.p0 + gl] : 0.f;
+        t2 = t + nwarps;
+        next2 = load_meta(a, P, t2 < ntup && e_lane + t2 * C < e1 ? L.list[e_lane + t2 * C] : -1);
+        uint32_t Np = cm.Np, Nt = cm.Nt;
+        const int cell = cm.cell, p0 = cm.p0, t0 = cm.t0, mat = cm.mat;
+        bool active = Np != 0 && Nt != 0;
+        if (active && (unsigned)mat >= (unsigned)a.n_mat) {
+            if (gl == 0) atomicOr(&bacc.status, PCC_ST_NONFINITE);
+            active = false;
+        }
+        if constexpr (G == 32) {   // one cell per warp: warp-uniform
+            if (!active) continue;
+        } else {
+            if (!active) Np = Nt = 0;
+            if (!__any_sync(kFull, active)) continue;
+        }
+        const bool caseA = Np >= Nt;
+        // ---- sums (the first G weights of each list were prefetched)
+        const float w0 = __shfl_sync(kFull, tw0, 0, G);
+        float sp = 0.f, st = 0.f, sf = 0.f;
+        bool uni = true;
+#pragma unroll 4
+        for (uint32_t s = gl; s < Nt; s += G) {
+            const float wt = s < (uint32_t)G ? tw0 : I.w[t0 + s];
+            st += wt;
+            uni &= (wt == w0);
+        }
+        if (caseA) {
+#pragma unroll 4
+            for (uint32_t s = gl; s < Np; s += G) {
+                const float wp = s < (uint32_t)G ? pw0 : P.w[p0 + s];
+                sp += wp;
+                sf += fminf(wp, w0);
+            }
+        } else {   // projectile s takes part in ceil((N_t - s) / N_p) pairs
+            for (uint32_t s = gl; s < Np; s += G) {
+                const float wp = s < (uint32_t)G ? pw0 : P.w[p0 + s];
+                sp += wp;
+                sf += fminf(wp, w0) * (float)((Nt - s + Np - 1) / Np);
+            }
+        }
+        const float n_p = group_sum<G>(sp), n_t = group_sum<G>(st);
+        float n_pt;
+        if constexpr (G == 32) {
+            n_pt = __all_sync(kFull, uni) ? warp_sum(sf) : npt_over_pairs<GROUP>(a, P, cell, p0, t0, Np, Nt, tab, lane);
+        } else {
+            n_pt = group_sum<G>(sf);
+            // unequal target weights: n_pt over the actual pairs, one such
+            // cell at a time with the whole warp
+            unsigned odd = __ballot_sync(kFull, !uni);
+            odd = __ballot_sync(kFull, active && gl == 0 && (odd & gmask) != 0u);
+            while (odd) {
+                const int src = __ffs(odd) - 1;
+                odd &= odd - 1u;
+                const float v = npt_over_pairs<GROUP>(a, P, __shfl_sync(kFull, cell, src),
+                                                      __shfl_sync(kFull, p0, src), __shfl_sync(kFull, t0, src),
+                                                      __shfl_sync(kFull, Np, src), __shfl_sync(kFull, Nt, src), tab,
+                                                      lane);
+                if (gi == src / G) n_pt = v;
+            }
+        }
+        const float coef = __fdividef(n_p, n_pt) * n_t * a.f_cdt;
+        uint32_t k1 = 0, k2 = 0;
+        if (active) bound_thresholds<GROUP>(a, mat, coef, k1, k2);
+        uint32_t ncand = 0;   // candidates of this lane's cell (uniform over its group)
+        // ---- cells with N_p >= N_t: one pair per projectile slot
+        const uint32_t itA = active && caseA ? (Np + 2 * G - 1) / (2 * G) : 0u;
+        const uint32_t nitA = G == 32 ? itA : __reduce_max_sync(kFull, itA);
+        const uint32_t tag0 = stream_tag(GROUP, kAccept, 0);
+        for (uint32_t it = 0; it < nitA; ++it) {
+            const uint32_t base = it * (2 * G);
+            const Philox4 ph = draw_k((base >> 1) + gl, (uint32_t)cell, step32, tag0, a.keys);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t s = base + 2 * gl + h;
+                const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
+                const bool cand = (G == 32 || it < itA) && s < Np && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
+                const unsigned m = __ballot_sync(kFull, cand);
+                if (cand) wb[sw.nb + __popc(m & below)] = make_uint2((uint32_t)cell, s);
+                sw.nb += __popc(m);
+                ncand += __popc(m & gmask);
+            }
+            if (sw.nb > kWarpBuf - 64) {   // flush the staging buffer to the flat queue
+                flush_staged(Q, wb, sw.nb, bacc, lane);
+                sw.nb = 0;
+            }
+        }
+        // ---- cells with N_p < N_t.  Draw units (pass m, slot pair q): unit
+        // i = m Qn + q covers slots 2q and 2q+1 of pass m, i.e. pairs
+        // j = s + m N_p.  A group's lanes take consecutive units, so each
+        // projectile's pairs are queued in increasing j.
+        const uint32_t Qn = (Np + 1) >> 1, passes = Np ? (Nt + Np - 1) / Np : 0u, units = Qn * passes;
+        const uint32_t itB = active && !caseA ? (units + G - 1) / G : 0u;
+        const uint32_t nitB = G == 32 ? itB : __reduce_max_sync(kFull, itB);
+        uint32_t cnt = 0;
+        for (uint32_t it = 0; it < nitB; ++it) {
+            const uint32_t i = it * G + gl;
+            const bool valid = (G == 32 || it < itB) && i < units;
+            const uint32_t mp = valid ? i / Qn : 0u, q = valid ? i - mp * Qn : 0u;
+            const Philox4 ph = draw_k(q, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t s = 2 * q + h, j = s + mp * Np;
+                const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
+                const bool cand = valid && s < Np && j < Nt && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
+                const unsigned m = __ballot_sync(kFull, cand);
+                if (cand) Q.qb[t0 + cnt + __popc(m & gmask & below)] = j;
+                cnt += __popc(m & gmask);
+            }
+        }
+        if (!caseA) ncand = cnt;
+        if (gl == 0 && active) {
+            if (!caseA) {
+                Q.cand[cell] = (int)cnt;
+                if (cnt) Q.caseb[atomicAdd(Q.caseb_count, 1)] = cell;
+            }
+            if (ncand) {
+                Q.rec[2 * (size_t)cell] = make_int4(p0, t0, (int)Np, (int)Nt);
+                Q.rec[2 * (size_t)cell + 1] = make_int4(mat, __float_as_int(coef), 0, 0);
+            }
+            sw.npairs += caseA ? Np : Nt;
+            sw.ncands += ncand;
+            if ((caseA ? Np : Nt) > 65536u || (uint32_t)cell > 0xFFFFFFu || a.step > 0x7FFFFull)
+                atomicOr(&bacc.status, PCC_ST_ID_RANGE);
+        }
+    }
+}
+
+// Lane-group width by size class (class k: N_pair in [2^(k-1), 2^k)), per
+// group: classes from `warp` up take a whole warp, [g16, warp) 16 lanes,
+// [g8, g16) 8 lanes, [g4, g8) 4 lanes, and the smaller ones 2 lanes.
+// Chosen by timing each group on the 2^20-cell batched Cu workload.
+template <int GROUP> struct ScanClass;
+template <> struct ScanClass<kGroupEm> { static constexpr int warp = 11, g16 = 10, g8 = 8, g4 = 1; };
+template <> struct ScanClass<kGroupEp> { static constexpr int warp = 7, g16 = 7, g8 = 4, g4 = 1; };
+template <> struct ScanClass<kGroupPh> { static constexpr int warp = 10, g16 = 9, g8 = 8, g4 = 7; };
+
+// Scan: for each cell, the sums n_p, n_t, n_pt of Sec. III.A, the
 // coefficient, and the accept uniforms of every pair against the
 // per-material bounds.  Pairs at or above the bounds are rejected here,
 // exactly (U >= bound >= x >= 1 - exp(-x)), without reading the particle
-// records; the others are queued.  Lane l owns slots base + 2l and
-// base + 2l + 1, whose uniforms are the four words of its own Philox draw.
-// Contains no calls, so its loop state stays in registers.
+// records; the others are queued.  The list holds the size classes from the
+// largest (class k: N_pair in [2^(k-1), 2^k)); the largest cells take a
+// whole warp, smaller ones a group of 16, 8, 4 or 2 lanes (ScanClass), so
+// that the per-cell work (metadata, sums, coefficient, record) is shared by
+// up to 16 cells per warp instruction.  Contains no calls, so its loop state
+// stays in registers.
 template <int GROUP, int MINB>
 __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __grid_constant__ StepArgs a, CellList L,
                                                                      Queue Q)
@@ -1098,175 +1342,38 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* tab = scratch[wid];
     uint2* wb = buf[wid];
-    int nb = 0;   // staged candidates of this warp (warp-uniform)
-    unsigned long long npairs = 0, ncands = 0;   // lane 0's counts
-    int n = 0;
-    for (int k = 0; k < kClasses; ++k) n += L.hist[k];
+    // segment ends: whole warps, then 16-, 8-, 4- and 2-lane groups
+    int e32 = 0, e16 = 0, e8 = 0, e4 = 0, e2 = 0;
+    for (int k = kClasses - 1; k >= 0; --k) {
+        const int h = L.hist[k];
+        if (k >= ScanClass<GROUP>::warp) e32 += h;
+        else if (k >= ScanClass<GROUP>::g16) e16 += h;
+        else if (k >= ScanClass<GROUP>::g8) e8 += h;
+        else if (k >= ScanClass<GROUP>::g4) e4 += h;
+        else e2 += h;
+    }
+    e16 += e32;
+    e8 += e16;
+    e4 += e8;
+    e2 += e4;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    const SpeciesView& P = GROUP == kGroupEm ? a.em : (GROUP == kGroupEp ? a.ep : a.ph);
-    const SpeciesView& I = a.ion;
-    const uint32_t step32 = (uint32_t)a.step;
-    // Two-stage prefetch: the metadata of the cell after next, and the first
-    // 32 weights of both lists of the next cell, load while a cell is scanned.
-    int kk = blockIdx.x * (blockDim.x >> 5) + wid;
-    CellMeta next = load_meta(a, P, kk < n ? L.list[kk] : -1);
-    float next_tw = (uint32_t)lane < next.Nt ? I.w[next.t0 + lane] : 0.f;
-    float next_pw = (uint32_t)lane < next.Np ? P.w[next.p0 + lane] : 0.f;
-    CellMeta next2 = load_meta(a, P, kk + nwarps < n ? L.list[kk + nwarps] : -1);
-    while (kk < n) {
-        const CellMeta cm = next;
-        const float tw0 = next_tw, pw0 = next_pw;   // weights of slots lane of this cell
-        kk += nwarps;
-        next = next2;
-        next_tw = (uint32_t)lane < next.Nt ? I.w[next.t0 + lane] : 0.f;
-        next_pw = (uint32_t)lane < next.Np ? P.w[next.p0 + lane] : 0.f;
-        next2 = load_meta(a, P, kk + nwarps < n ? L.list[kk + nwarps] : -1);
-        const uint32_t Np = cm.Np, Nt = cm.Nt;
-        const int cell = cm.cell, p0 = cm.p0, t0 = cm.t0, mat = cm.mat;
-        if (Np == 0 || Nt == 0) continue;
-        if ((unsigned)mat >= (unsigned)a.n_mat) {
-            if (lane == 0) atomicOr(&bacc.status, PCC_ST_NONFINITE);
-            continue;
-        }
-        const bool caseA = Np >= Nt;
-        // ---- sums (the first 32 weights of each list were prefetched)
-        const float w0 = __shfl_sync(0xffffffffu, tw0, 0);
-        float sp = 0.f, st = 0.f, sf = 0.f;
-        bool uni = true;
-#pragma unroll 4
-        for (uint32_t s = lane; s < Nt; s += 32) {
-            const float wt = s < 32u ? tw0 : I.w[t0 + s];
-            st += wt;
-            uni &= (wt == w0);
-        }
-        if (caseA) {
-#pragma unroll 4
-            for (uint32_t s = lane; s < Np; s += 32) {
-                const float wp = s < 32u ? pw0 : P.w[p0 + s];
-                sp += wp;
-                sf += fminf(wp, w0);
-            }
-        } else {   // projectile s takes part in ceil((N_t - s) / N_p) pairs
-            for (uint32_t s = lane; s < Np; s += 32) {
-                const float wp = s < 32u ? pw0 : P.w[p0 + s];
-                sp += wp;
-                sf += fminf(wp, w0) * (float)((Nt - s + Np - 1) / Np);
-            }
-        }
-        const float n_p = warp_sum(sp), n_t = warp_sum(st);
-        float n_pt;
-        if (__all_sync(0xffffffffu, uni)) {
-            n_pt = warp_sum(sf);
-        } else {   // unequal target weights: sum over the actual pairs
-            const Philox4 kp = draw_k(0, (uint32_t)cell, step32, stream_tag(GROUP, kPerm, 0), a.keys);
-            PermKeys rk;
-            rk.k[0] = kp.v[0]; rk.k[1] = kp.v[1]; rk.k[2] = kp.v[2]; rk.k[3] = kp.v[3];
-            const uint32_t NL = caseA ? Np : Nt;
-            if (NL <= 32) {
-                __syncwarp();
-                if (lane < (int)NL) {
-                    const uint32_t r = perm_pos_small(lane, NL, rk);
-                    tab[r] = lane;    // P table
-                    tab[32 + lane] = r;
-                }
-                __syncwarp();
-            }
-            float spt = 0.f;
-            const float inv_nt = 1.0f / (float)Nt;
-            if (caseA) {
-                for (uint32_t s = lane; s < Np; s += 32) {
-                    const uint32_t j = NL <= 32 ? (uint32_t)tab[32 + s] : perm_pos_large(s, Np, rk);
-                    spt += fminf(P.w[p0 + s], I.w[t0 + fast_mod(j, Nt, inv_nt)]);
-                }
-            } else {   // lanes over the pairs: projectile j mod N_p, target P(j)
-                for (uint32_t j = lane; j < Nt; j += 32) {
-                    const uint32_t t = NL <= 32 ? (uint32_t)tab[j] : perm_elem_large(j, Nt, rk);
-                    spt += fminf(P.w[p0 + j % Np], I.w[t0 + t]);
-                }
-            }
-            n_pt = warp_sum(spt);
-        }
-        const float coef = __fdividef(n_p, n_pt) * n_t * a.f_cdt;
-        uint32_t k1, k2;
-        bound_thresholds<GROUP>(a, mat, coef, k1, k2);
-        const uint32_t tag0 = stream_tag(GROUP, kAccept, 0);
-        uint32_t ncand = 0;
-        if (caseA) {
-            for (uint32_t base = 0; base < Np; base += 64) {
-                const Philox4 ph = draw_k((base >> 1) + lane, (uint32_t)cell, step32, tag0, a.keys);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t s = base + 2 * lane + h;
-                    const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
-                    const bool cand = s < Np && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
-                    const unsigned m = __ballot_sync(0xffffffffu, cand);
-                    if (cand) wb[nb + __popc(m & ((1u << lane) - 1u))] = make_uint2((uint32_t)cell, s);
-                    nb += __popc(m);
-                    ncand += __popc(m);
-                }
-                if (nb > kWarpBuf - 64) {   // flush the staging buffer to the flat queue
-                    __syncwarp();
-                    int base_q = 0;
-                    if (lane == 0) base_q = atomicAdd(Q.flat_count, nb);
-                    base_q = __shfl_sync(0xffffffffu, base_q, 0);
-                    for (int i = lane; i < nb; i += 32)
-                        if ((uint32_t)(base_q + i) < Q.cap_flat) Q.flat[base_q + i] = wb[i];
-                    if (lane == 0 && (uint32_t)(base_q + nb) > Q.cap_flat) atomicOr(&bacc.status, PCC_ST_CAPACITY);
-                    nb = 0;
-                    __syncwarp();
-                }
-            }
-        } else {
-            // Draw units (pass m, slot pair q): unit i = m Qn + q covers slots 2q and
-            // 2q+1 of pass m, i.e. pairs j = s + m N_p.  Lanes take consecutive
-            // units, so each projectile's pairs are queued in increasing j.
-            uint32_t cnt = 0;
-            const uint32_t Qn = (Np + 1) >> 1, passes = (Nt + Np - 1) / Np, units = Qn * passes;
-            for (uint32_t i0 = 0; i0 < units; i0 += 32) {
-                const uint32_t i = i0 + lane;
-                const bool valid = i < units;
-                const uint32_t mp = valid ? i / Qn : 0u, q = valid ? i - mp * Qn : 0u;
-                const Philox4 ph = draw_k(q, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t s = 2 * q + h, j = s + mp * Np;
-                    const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
-                    const bool cand = valid && s < Np && j < Nt && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
-                    const unsigned m = __ballot_sync(0xffffffffu, cand);
-                    if (cand) Q.qb[t0 + cnt + __popc(m & ((1u << lane) - 1u))] = j;
-                    cnt += __popc(m);
-                }
-            }
-            if (lane == 0) {
-                Q.cand[cell] = (int)cnt;
-                if (cnt) Q.caseb[atomicAdd(Q.caseb_count, 1)] = cell;
-            }
-            ncand = cnt;
-        }
-        if (lane == 0) {
-            if (ncand) {
-                Q.rec[2 * (size_t)cell] = make_int4(cm.p0, t0, (int)Np, (int)Nt);
-                Q.rec[2 * (size_t)cell + 1] = make_int4(mat, __float_as_int(coef), 0, 0);
-            }
-            npairs += caseA ? Np : Nt;
-            ncands += ncand;
-            if ((caseA ? Np : Nt) > 65536u || (uint32_t)cell > 0xFFFFFFu || a.step > 0x7FFFFull)
-                atomicOr(&bacc.status, PCC_ST_ID_RANGE);
-        }
-    }
-    if (nb > 0) {   // final flush
-        __syncwarp();
-        int base_q = 0;
-        if (lane == 0) base_q = atomicAdd(Q.flat_count, nb);
-        base_q = __shfl_sync(0xffffffffu, base_q, 0);
-        for (int i = lane; i < nb; i += 32)
-            if ((uint32_t)(base_q + i) < Q.cap_flat) Q.flat[base_q + i] = wb[i];
-        if (lane == 0 && (uint32_t)(base_q + nb) > Q.cap_flat) atomicOr(&bacc.status, PCC_ST_CAPACITY);
-    }
-    if (lane == 0) {
-        if (npairs) atomicAdd(&bacc.pairs[GROUP], npairs);
-        if (ncands) atomicAdd(&bacc.candidates[GROUP], ncands);
-    }
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wid;
+    ScanWarp sw{0, 0ull, 0ull};
+    // the round-robin continues across segments: a segment's first tuple
+    // goes to the warp after the one that took the previous segment's last
+    int d = 0;
+    scan_segment<GROUP, 32>(a, L, Q, 0, e32, gw, nwarps, tab, wb, sw, bacc);
+    d = (d + e32) % nwarps;
+    scan_segment<GROUP, 16>(a, L, Q, e32, e16, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw, bacc);
+    d = (d + (e16 - e32 + 1) / 2) % nwarps;
+    scan_segment<GROUP, 8>(a, L, Q, e16, e8, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw, bacc);
+    d = (d + (e8 - e16 + 3) / 4) % nwarps;
+    scan_segment<GROUP, 4>(a, L, Q, e8, e4, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw, bacc);
+    d = (d + (e4 - e8 + 7) / 8) % nwarps;
+    scan_segment<GROUP, 2>(a, L, Q, e4, e2, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw, bacc);
+    if (sw.nb > 0) flush_staged(Q, wb, sw.nb, bacc, lane);   // final flush
+    if (sw.npairs) atomicAdd(&bacc.pairs[GROUP], sw.npairs);
+    if (sw.ncands) atomicAdd(&bacc.candidates[GROUP], sw.ncands);
     __syncthreads();
     block_acc_flush(bacc, a.st);
 }
