@@ -821,9 +821,7 @@ __global__ void __launch_bounds__(1024) class_offsets_kernel(CellList L)
 {
     extern __shared__ int sm[];
     __shared__ int part[1024];
-    __shared__ int tot[kClasses];
     const int n = kClasses * L.nblk;
-    if (threadIdx.x < kClasses) tot[threadIdx.x] = 0;
     int* v = SMEM ? sm : L.bh;
     if (SMEM)
         for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = L.bh[i];
@@ -833,12 +831,7 @@ __global__ void __launch_bounds__(1024) class_offsets_kernel(CellList L)
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int i0 = threadIdx.x * per, i1 = min(i0 + per, n);
     int sum = 0;
-    for (int e = i0; e < i1; ++e) {
-        const int k = kClasses - 1 - e / L.nblk;
-        const int x = v[k * L.nblk + e % L.nblk];
-        sum += x;
-        if (x) atomicAdd(&tot[k], x);
-    }
+    for (int e = i0; e < i1; ++e) sum += v[(kClasses - 1 - e / L.nblk) * L.nblk + e % L.nblk];
     part[threadIdx.x] = sum;
     __syncthreads();
     for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive scan of the thread sums
@@ -855,9 +848,15 @@ __global__ void __launch_bounds__(1024) class_offsets_kernel(CellList L)
         run += c;
     }
     __syncthreads();
+    // class k occupies [offset of its block 0, offset of block 0 of class
+    // k - 1) of the list; class 0 ends at the total
+    if (threadIdx.x < kClasses) {
+        const int k = threadIdx.x;
+        const int end = k == 0 ? part[blockDim.x - 1] : v[(k - 1) * L.nblk];
+        L.hist[k] = end - v[k * L.nblk];
+    }
     if (SMEM)
         for (int i = threadIdx.x; i < n; i += blockDim.x) L.bh[i] = sm[i];
-    if (threadIdx.x < kClasses) L.hist[threadIdx.x] = tot[threadIdx.x];
 }
 
 __global__ void class_scatter_kernel(const int* __restrict__ cnt_p, const int* __restrict__ cnt_t, int n_cells,
@@ -1537,38 +1536,63 @@ __global__ void __launch_bounds__(kBatchedThreads, 2) caseb_cand_kernel(const __
 
 // Stable removal of the absorbed photons (weight 0) from the first Np slots
 // of a cell region, keeping the order of the rest (including the Np..n_all
-// secondaries appended in this step), one warp: each 32-record chunk is read
-// into registers before any write, and destinations never pass sources.
+// secondaries appended in this step), one warp.  The records before the
+// first removed one are not touched; from there each batch of 4 x 32
+// records is read into registers before any of it is written, and
+// destinations never pass sources.
 __device__ void compact_region_warp(const SpeciesView& P, int cell)
 {
+    constexpr unsigned kFull = 0xffffffffu;
+    constexpr int kU = 4;   // 32-record chunks loaded before any of them is stored
     const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
     const int p0 = P.start[cell], Np = P.count[cell];
     const int n_all = Np + P.added[cell];
     const bool has_x = P.x != nullptr;
-    int wr = 0;   // warp-uniform write position
-    for (int c0 = 0; c0 < n_all; c0 += 32) {
-        const int i = c0 + lane;
-        const bool in = i < n_all;
-        float ux = 0.f, uy = 0.f, uz = 0.f, w = 0.f, x = 0.f;
-        uint64_t pid = 0;
-        if (in) {
-            const int src = p0 + i;
-            ux = P.ux[src]; uy = P.uy[src]; uz = P.uz[src]; w = P.w[src];
-            if (has_x) x = P.x[src];
-            pid = P.pid[src];
+    // the records before the first removed one stay where they are
+    int c0 = 0;
+    for (; c0 < Np; c0 += 32 * kU) {
+        bool hole = false;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = c0 + 32 * u + lane;
+            if (i < Np) hole |= P.w[p0 + i] == 0.f;
         }
-        const bool keep = in && !(i < Np && w == 0.f);
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        __syncwarp();
-        if (keep) {
-            const int dst = p0 + wr + __popc(m & ((1u << lane) - 1u));
-            if (dst != p0 + i) {
-                P.ux[dst] = ux; P.uy[dst] = uy; P.uz[dst] = uz; P.w[dst] = w;
-                if (has_x) P.x[dst] = x;
-                P.pid[dst] = pid;
+        if (__any_sync(kFull, hole)) break;
+    }
+    if (c0 >= Np) return;   // nothing removed
+    int wr = c0;            // warp-uniform write position
+    for (int b = c0; b < n_all; b += 32 * kU) {
+        float ux[kU], uy[kU], uz[kU], w[kU], x[kU];
+        uint64_t pid[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = b + 32 * u + lane;
+            ux[u] = uy[u] = uz[u] = w[u] = x[u] = 0.f;
+            pid[u] = 0;
+            if (i < n_all) {
+                const int src = p0 + i;
+                ux[u] = P.ux[src]; uy[u] = P.uy[src]; uz[u] = P.uz[src]; w[u] = P.w[src];
+                if (has_x) x[u] = P.x[src];
+                pid[u] = P.pid[src];
             }
         }
-        wr += __popc(m);
+        __syncwarp();   // every record of the batch is read before any is overwritten
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = b + 32 * u + lane;
+            const bool keep = i < n_all && !(i < Np && w[u] == 0.f);
+            const unsigned m = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int dst = p0 + wr + __popc(m & below);
+                if (dst != p0 + i) {
+                    P.ux[dst] = ux[u]; P.uy[dst] = uy[u]; P.uz[dst] = uz[u]; P.w[dst] = w[u];
+                    if (has_x) P.x[dst] = x[u];
+                    P.pid[dst] = pid[u];
+                }
+            }
+            wr += __popc(m);
+        }
         __syncwarp();
     }
     if (lane == 0) P.count[cell] = wr - P.added[cell];
