@@ -194,7 +194,8 @@ int pcc_collide(pcc_ctx *ctx, const pcc_cells *cells, pcc_species *em, pcc_speci
 
 /* Launch schedule of the batched FP32 collision kernels (no counterpart in
  * the paper; a performance setting that never changes results).  Cells are
- * processed one per warp, largest size class first; min_blocks_per_sm
+ * scanned largest size class first, a warp for each large cell and a group
+ * of 16 to 2 lanes for each smaller one; min_blocks_per_sm
  * (2 to 6) selects the register budget of the kernel (a minimum of that
  * many resident 256-thread blocks per SM) and blocks_per_sm caps the
  * persistent grid (0 = as many as fit).  Applies to later pcc_collide calls
@@ -239,16 +240,18 @@ int pcc_totals_noalloc(int n_cells, const pcc_species *sp, int is_photon, double
 
 /* The multi-step collision loop as one CUDA graph (the batching pattern
  * around Sec. III.A's per-step procedure).  One captured step is:
- * pcc_collide for each group of the mask in the order e-, e+, photons
- * (each as its own call with the matching PCC_GROUP_* bit), then
- * pcc_append_secondaries for e-, e+ and photons.  pcc_steps_capture records
+ * the work of one pcc_collide call with the descriptor's mask (groups in
+ * the order e-, e+, photons), then pcc_append_secondaries for e-, e+ and
+ * photons.  pcc_steps_capture records
  * n_steps such steps, for step indices step0 .. step0 + n_steps - 1, into a
  * graph owned by the context (replacing any earlier one); every allocation
  * the steps need happens before the capture, which runs on a stream of the
  * context's own, so the caller's stream is not captured.  All pointers in
  * the descriptor must stay valid and unchanged while the graph is used.
  * timing != 0 adds five timing events per step (before the e- group, after
- * each group, after the commits), read by pcc_steps_timing.
+ * each group, after the commits), read by pcc_steps_timing; on the batched
+ * path the size-class sort of all groups runs before the e- group's kernels
+ * and is timed with them.
  * pcc_steps_launch enqueues the whole graph on the stream.  A launch
  * repeats the same step indices: capture again to go on. */
 typedef struct {

@@ -794,33 +794,56 @@ __device__ __forceinline__ int size_class(int np, int nt)
     return b < kClasses ? b : kClasses - 1;
 }
 
+// The class sorts of the three groups {e-, e+, photon} against the ions,
+// done together: the counts do not change during a collide call (secondaries
+// are committed after it), so one pass reads the ion counts once.
+struct ClassSort {
+    CellList L[3];
+    const int* cnt_p[3];   // projectile counts per group
+    const int* cnt_t;      // ion counts
+    int n_cells;
+    unsigned run;          // bit g: group g is sorted
+};
+
 // Counting sort of the cells with both species by decreasing size class,
 // in three passes without global atomics: per-block class counts, their
 // exclusive scan (classes from the largest, blocks in order), and the
-// scatter with ranks from shared-memory counters.
-__global__ void class_hist_kernel(const int* __restrict__ cnt_p, const int* __restrict__ cnt_t, int n_cells,
-                                  CellList L)
+// scatter with ranks from shared-memory counters.  The order within one
+// block's cells of one class follows the shared atomics and may differ from
+// run to run; no result depends on it, since every cell is processed
+// independently of where it sits in the list.
+__global__ void class_hist_kernel(const __grid_constant__ ClassSort S)
 {
-    __shared__ int h[kClasses];
-    if (threadIdx.x < kClasses) h[threadIdx.x] = 0;
+    __shared__ int h[3][kClasses];
+    for (int i = threadIdx.x; i < 3 * kClasses; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n_cells) {
-        const int np = cnt_p[c], nt = cnt_t[c];
-        if (np > 0 && nt > 0) atomicAdd(&h[size_class(np, nt)], 1);
+    if (c < S.n_cells) {
+        const int nt = S.cnt_t[c];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            if (!(S.run >> g & 1u) || nt <= 0) continue;
+            const int np = S.cnt_p[g][c];
+            if (np > 0) atomicAdd(&h[g][size_class(np, nt)], 1);
+        }
     }
     __syncthreads();
-    if (threadIdx.x < kClasses) L.bh[threadIdx.x * L.nblk + blockIdx.x] = h[threadIdx.x];
+    for (int i = threadIdx.x; i < 3 * kClasses; i += blockDim.x) {
+        const int g = i / kClasses, k = i - g * kClasses;
+        if (S.run >> g & 1u) S.L[g].bh[k * S.L[g].nblk + blockIdx.x] = h[g][k];
+    }
 }
 
-// One block: bh[k][b] -> offset of block b's cells of class k in the list;
-// hist[k] -> cells of class k.  The counts are staged in shared memory when
-// they fit (SMEM = true), else scanned in place in global memory.
+// One block per group: bh[k][b] -> offset of block b's cells of class k in
+// the list; hist[k] -> cells of class k.  The counts are staged in shared
+// memory when they fit (SMEM = true), else scanned in place in global memory.
 template <bool SMEM>
-__global__ void __launch_bounds__(1024) class_offsets_kernel(CellList L)
+__global__ void __launch_bounds__(1024) class_offsets_kernel(const __grid_constant__ ClassSort S)
 {
     extern __shared__ int sm[];
     __shared__ int part[1024];
+    if (!(S.run >> blockIdx.x & 1u)) return;
+    const CellList& L = S.L[blockIdx.x];
     const int n = kClasses * L.nblk;
     int* v = SMEM ? sm : L.bh;
     if (SMEM)
@@ -859,18 +882,23 @@ __global__ void __launch_bounds__(1024) class_offsets_kernel(CellList L)
         for (int i = threadIdx.x; i < n; i += blockDim.x) L.bh[i] = sm[i];
 }
 
-__global__ void class_scatter_kernel(const int* __restrict__ cnt_p, const int* __restrict__ cnt_t, int n_cells,
-                                     CellList L)
+__global__ void class_scatter_kernel(const __grid_constant__ ClassSort S)
 {
-    __shared__ int rank[kClasses];
-    if (threadIdx.x < kClasses) rank[threadIdx.x] = 0;
+    __shared__ int rank[3][kClasses];
+    for (int i = threadIdx.x; i < 3 * kClasses; i += blockDim.x) (&rank[0][0])[i] = 0;
     __syncthreads();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n_cells) {
-        const int np = cnt_p[c], nt = cnt_t[c];
-        if (np > 0 && nt > 0) {
-            const int cls = size_class(np, nt);
-            L.list[L.bh[cls * L.nblk + blockIdx.x] + atomicAdd(&rank[cls], 1)] = c;
+    if (c < S.n_cells) {
+        const int nt = S.cnt_t[c];
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+            if (!(S.run >> g & 1u) || nt <= 0) continue;
+            const int np = S.cnt_p[g][c];
+            if (np > 0) {
+                const int cls = size_class(np, nt);
+                const CellList& L = S.L[g];
+                L.list[L.bh[cls * L.nblk + blockIdx.x] + atomicAdd(&rank[g][cls], 1)] = c;
+            }
         }
     }
 }
@@ -1717,7 +1745,7 @@ static int persistent_grid(pcc_ctx* ctx, const void* fn, int smem, int want_per_
 //   [8n, 10n) ledger contributions (float2)  [R, R + 8n) cell records (int4 pairs,
 //   R = 10n rounded up to 4 ints)           [R + 8n) class histograms and cursors,
 //   then three counters (flat queue, N_p < N_t cells, cells with events), then
-//   the per-block class counts of the group being sorted.
+//   the per-block class counts of the three groups.
 // Flags and contributions start at zero and are cleared by the finalize kernel.
 static size_t rec_off(size_t n) { return (10 * n + 3) & ~(size_t)3; }
 static size_t hist_off(size_t n) { return rec_off(n) + 8 * n; }
@@ -1729,7 +1757,7 @@ static int ensure_lists(pcc_ctx* ctx, int n_cells)
     ctx->lists = nullptr;
     ctx->lists_cells = 0;
     const size_t nblk = ((size_t)n_cells + kClassBlock - 1) / kClassBlock;
-    const size_t bytes = (hist_off(n_cells) + 6 * kClasses + 8 + kClasses * nblk) * sizeof(int);
+    const size_t bytes = (hist_off(n_cells) + 6 * kClasses + 8 + 3 * kClasses * nblk) * sizeof(int);
     cudaError_t e = cudaMalloc(&ctx->lists, bytes);
     if (e == cudaSuccess) e = cudaMemset(ctx->lists, 0, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: cell lists");
@@ -1766,7 +1794,7 @@ static CellList list_of(pcc_ctx* ctx, int group)
     L.hist = ctx->lists + hist_off(n) + (size_t)(2 * group) * kClasses;
     L.cursor = L.hist + kClasses;
     L.nblk = (int)((n + kClassBlock - 1) / kClassBlock);
-    L.bh = ctx->lists + hist_off(n) + 6 * kClasses + 8;   // shared by the groups (used in turn)
+    L.bh = ctx->lists + hist_off(n) + 6 * kClasses + 8 + (size_t)group * kClasses * L.nblk;
     return L;
 }
 
@@ -1799,20 +1827,16 @@ static void launch_scan(pcc_ctx* ctx, const StepArgs& a, const CellList& L, cons
     scan_kernel<GROUP, MINB><<<g, kBatchedThreads, 0, st>>>(a, L, Q);
 }
 
-// Per group: counters, size classes, scan (register budget chosen by the
-// schedule: 2, 3 or 4 resident blocks per SM), candidates, finalize.
+// Per group, after the class sort of all groups: counters, scan (register
+// budget chosen by the schedule: 2 to 6 resident blocks per SM),
+// candidates, finalize.
 template <int GROUP>
-static cudaError_t launch_batched(pcc_ctx* ctx, const StepArgs& a, const SpeciesView& P, int stage, cudaStream_t st)
+static cudaError_t launch_batched(pcc_ctx* ctx, const StepArgs& a, int stage, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(counters_of(ctx), 0, 3 * sizeof(int), st);
     if (e != cudaSuccess) return e;
     const CellList L = list_of(ctx, GROUP);
     const Queue Q = queue_of(ctx);
-    class_hist_kernel<<<L.nblk, kClassBlock, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
-    const size_t off_smem = (size_t)kClasses * L.nblk * sizeof(int);
-    if (off_smem <= (size_t)kClassSmemMax) class_offsets_kernel<true><<<1, 1024, off_smem, st>>>(L);
-    else class_offsets_kernel<false><<<1, 1024, 0, st>>>(L);
-    class_scatter_kernel<<<L.nblk, kClassBlock, 0, st>>>(P.count, a.ion.count, a.n_cells, L);
     switch (ctx->minb) {
     case 2: launch_scan<GROUP, 2>(ctx, a, L, Q, st); break;
     case 3: launch_scan<GROUP, 3>(ctx, a, L, Q, st); break;
@@ -1825,8 +1849,28 @@ static cudaError_t launch_batched(pcc_ctx* ctx, const StepArgs& a, const Species
     const int gb = persistent_grid(ctx, (const void*)caseb_cand_kernel<GROUP>, stage, 0);
     caseb_cand_kernel<GROUP><<<gb, kBatchedThreads, stage, st>>>(a, Q, stage);
     finalize_kernel<GROUP><<<2 * std::max(ctx->num_sms, 1), 256, 0, st>>>(a, Q);
-    note_launches(7);
+    note_launches(4);
     return cudaSuccess;
+}
+
+// The size-class lists of the groups that run, in three launches.
+static void launch_class_sort(pcc_ctx* ctx, const StepArgs& a, unsigned run, cudaStream_t st)
+{
+    ClassSort S;
+    for (int g = 0; g < 3; ++g) S.L[g] = list_of(ctx, g);
+    S.cnt_p[0] = a.em.count;
+    S.cnt_p[1] = a.ep.count;
+    S.cnt_p[2] = a.ph.count;
+    S.cnt_t = a.ion.count;
+    S.n_cells = a.n_cells;
+    S.run = run;
+    const int nblk = S.L[0].nblk;
+    class_hist_kernel<<<nblk, kClassBlock, 0, st>>>(S);
+    const size_t off_smem = (size_t)kClasses * nblk * sizeof(int);
+    if (off_smem <= (size_t)kClassSmemMax) class_offsets_kernel<true><<<3, 1024, off_smem, st>>>(S);
+    else class_offsets_kernel<false><<<3, 1024, 0, st>>>(S);
+    class_scatter_kernel<<<nblk, kClassBlock, 0, st>>>(S);
+    note_launches(3);
 }
 
 static int table_stage_bytes(const pcc_ctx* ctx)
@@ -1893,9 +1937,9 @@ extern "C" int pcc_set_schedule(pcc_ctx* ctx, int min_blocks_per_sm, int blocks_
     return PCC_OK;
 }
 
-extern "C" int pcc_collide(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em, pcc_species* ep, pcc_species* ph,
-                           const pcc_species* ion, double dt, uint64_t seed, uint64_t step, unsigned mask,
-                           int precision, float* ledger, void* stream)
+int collide_groups(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em, pcc_species* ep, pcc_species* ph,
+                   const pcc_species* ion, double dt, uint64_t seed, uint64_t step, unsigned mask, int precision,
+                   float* ledger, cudaStream_t st, int (*after_group)(void* user, int group), void* user)
 {
     if (!ctx || !cells || !cells->material_of_cell || cells->n_cells < 1) {
         set_error("pcc_collide: invalid cells");
@@ -1914,32 +1958,51 @@ extern "C" int pcc_collide(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em
         return PCC_E_INVALID;
     }
     if (ctx->n_mat == 0) { set_error("pcc_collide: tables not built"); return PCC_E_NO_TABLES; }
-    cudaStream_t st = (cudaStream_t)stream;
     StepArgs a = make_args(ctx, cells, em, ep, ph, ion, dt, seed, step, mask, ledger);
     const unsigned groups = (mask & 0x700u) ? (mask & 0x700u) : 0x700u;
     const bool ei = (mask & (PCC_BREMS | PCC_TRIDENT)) != 0, bh = (mask & PCC_BH) != 0;
     const bool run_em = ei && (groups & PCC_GROUP_EM), run_ep = ei && (groups & PCC_GROUP_EP);
     const bool run_ph = bh && (groups & PCC_GROUP_PH);
     a.mask = mask & 7u;
-    if (precision == PCC_FP64_PLAIN) {
-        if (run_em) collide_plain_kernel<kGroupEm><<<cells->n_cells, 128, 0, st>>>(a);
-        if (run_ep) collide_plain_kernel<kGroupEp><<<cells->n_cells, 128, 0, st>>>(a);
-        if (run_ph) collide_plain_kernel<kGroupPh><<<cells->n_cells, 128, 0, st>>>(a);
-        note_launches((unsigned)run_em + (unsigned)run_ep + (unsigned)run_ph);
-    } else {
+    const bool run[3] = {run_em, run_ep, run_ph};
+    int stage = 0;
+    if (precision == PCC_FP32_BATCHED) {
         int rc = collide_prepare(ctx, cells, em, ep, ph, ion, mask, precision);
         if (rc) return rc;
-        // zero the class histograms and cursors of the three groups (see list_of)
-        cudaError_t e = cudaMemsetAsync(ctx->lists + hist_off(ctx->lists_cells), 0, 6 * kClasses * sizeof(int), st);
-        if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: list counters");
-        const int stage = table_stage_bytes(ctx);
-        if (run_em && e == cudaSuccess) e = launch_batched<kGroupEm>(ctx, a, a.em, stage, st);
-        if (run_ep && e == cudaSuccess) e = launch_batched<kGroupEp>(ctx, a, a.ep, stage, st);
-        if (run_ph && e == cudaSuccess) e = launch_batched<kGroupPh>(ctx, a, a.ph, stage, st);
-        if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: batched launch");
+        launch_class_sort(ctx, a, (run_em ? 1u : 0u) | (run_ep ? 2u : 0u) | (run_ph ? 4u : 0u), st);
+        stage = table_stage_bytes(ctx);
+    }
+    for (int g = 0; g < 3; ++g) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: launch");
+        if (run[g]) {
+            if (precision == PCC_FP64_PLAIN) {
+                if (g == kGroupEm) collide_plain_kernel<kGroupEm><<<cells->n_cells, 128, 0, st>>>(a);
+                else if (g == kGroupEp) collide_plain_kernel<kGroupEp><<<cells->n_cells, 128, 0, st>>>(a);
+                else collide_plain_kernel<kGroupPh><<<cells->n_cells, 128, 0, st>>>(a);
+                note_launches(1);
+            } else {
+                if (g == kGroupEm) e = launch_batched<kGroupEm>(ctx, a, stage, st);
+                else if (g == kGroupEp) e = launch_batched<kGroupEp>(ctx, a, stage, st);
+                else e = launch_batched<kGroupPh>(ctx, a, stage, st);
+                if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: batched launch");
+            }
+        }
+        if (after_group) {
+            const int rc = after_group(user, g);
+            if (rc) return rc;
+        }
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PCC_OK : cuda_fail(e, "pcc_collide: launch");
+}
+
+extern "C" int pcc_collide(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em, pcc_species* ep, pcc_species* ph,
+                           const pcc_species* ion, double dt, uint64_t seed, uint64_t step, unsigned mask,
+                           int precision, float* ledger, void* stream)
+{
+    return collide_groups(ctx, cells, em, ep, ph, ion, dt, seed, step, mask, precision, ledger, (cudaStream_t)stream,
+                          nullptr, nullptr);
 }
 
 extern "C" int pcc_pairing(pcc_ctx* ctx, int n_cells, const pcc_species* proj, const pcc_species* targ, int group,

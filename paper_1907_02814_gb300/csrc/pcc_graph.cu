@@ -31,21 +31,28 @@ static int record(pcc_ctx* ctx, int idx, cudaStream_t cs)
     return e == cudaSuccess ? PCC_OK : cuda_fail(e, "pcc_steps_capture: event record");
 }
 
-// One step on the capture stream: the groups of the mask one by one, then
-// the three commits, with an event before and after each part.
+struct GroupEvents {
+    pcc_ctx* ctx;
+    int base;
+    cudaStream_t cs;
+};
+
+static int after_group(void* user, int g)
+{
+    const GroupEvents* r = static_cast<const GroupEvents*>(user);
+    return record(r->ctx, r->base + 1 + g, r->cs);
+}
+
+// One step on the capture stream: the groups of the mask one by one (the
+// batched path's class sort of all groups comes first, inside the first
+// part), then the three commits, with an event before and after each part.
 static int capture_step(pcc_ctx* ctx, const pcc_step_desc* d, uint64_t step, int s, cudaStream_t cs)
 {
-    const unsigned groups = (d->mask & 0x700u) ? (d->mask & 0x700u) : 0x700u;
-    const unsigned procs = d->mask & 7u;
-    const unsigned gbit[3] = {PCC_GROUP_EM, PCC_GROUP_EP, PCC_GROUP_PH};
+    GroupEvents ev{ctx, 5 * s, cs};
     int rc = record(ctx, 5 * s, cs);
-    for (int g = 0; g < 3 && rc == PCC_OK; ++g) {
-        const bool runs = (groups & gbit[g]) && (g < 2 ? (procs & (PCC_BREMS | PCC_TRIDENT)) : (procs & PCC_BH));
-        if (runs)
-            rc = pcc_collide(ctx, d->cells, d->em, d->ep, d->ph, d->ion, d->dt, d->seed, step, procs | gbit[g],
-                             d->precision, d->ledger, cs);
-        if (rc == PCC_OK) rc = record(ctx, 5 * s + 1 + g, cs);
-    }
+    if (rc == PCC_OK)
+        rc = collide_groups(ctx, d->cells, d->em, d->ep, d->ph, d->ion, d->dt, d->seed, step, d->mask, d->precision,
+                            d->ledger, cs, after_group, &ev);
     if (rc == PCC_OK) rc = pcc_append_secondaries(ctx, d->cells->n_cells, d->em, cs);
     if (rc == PCC_OK) rc = pcc_append_secondaries(ctx, d->cells->n_cells, d->ep, cs);
     if (rc == PCC_OK) rc = pcc_append_secondaries(ctx, d->cells->n_cells, d->ph, cs);

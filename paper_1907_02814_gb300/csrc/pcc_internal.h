@@ -84,4 +84,13 @@ TableGeom make_geom(const pcc_table_spec& s);
 // captured into a graph.
 int collide_prepare(pcc_ctx* ctx, const pcc_cells* cells, const pcc_species* em, const pcc_species* ep,
                     const pcc_species* ph, const pcc_species* ion, unsigned mask, int precision);
+// The work of pcc_collide on stream st.  After the kernels of group g
+// (0 e-, 1 e+, 2 photons) are enqueued, whether or not the group runs,
+// after_group(user, g) is called if given, so that a caller can record
+// events between the groups; a non-zero return ends the call with it.  The
+// batched path sorts the cells of every group that runs by size class
+// before the first group.
+int collide_groups(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em, pcc_species* ep, pcc_species* ph,
+                   const pcc_species* ion, double dt, uint64_t seed, uint64_t step, unsigned mask, int precision,
+                   float* ledger, cudaStream_t st, int (*after_group)(void* user, int group), void* user);
 void pcc_free_graph(pcc_ctx* ctx);

@@ -101,8 +101,9 @@ def test_graph_matches_eager_steps(pcc, ctx, precision):
 
 
 def test_launch_count(pcc, ctx):
-    """The counter adds 7 kernels per batched group, 1 per plain group, 1
-    per commit, and the kernel nodes of a graph per graph launch."""
+    """The counter adds 3 class-sort kernels and 4 per group for a batched
+    call, 1 per plain group, 1 per commit, and the kernel nodes of a graph
+    per graph launch."""
     wl = workload(n_cells=16, seed=12)
     tables(pcc, ctx, wl)
     mat = torch.as_tensor(wl.material_of_cell, device="cuda")
@@ -110,7 +111,7 @@ def test_launch_count(pcc, ctx):
     c0 = pcc.launch_count()
     pcc.collide(ctx, wl.n_cells, mat, wl.ion_mass, d["em"], d["ep"], d["ph"], d["ion"], wl.dt, wl.seed, 0,
                 precision=pcc.FP32_BATCHED)
-    assert pcc.launch_count() - c0 == 21
+    assert pcc.launch_count() - c0 == 3 + 3 * 4
     c0 = pcc.launch_count()
     pcc.collide(ctx, wl.n_cells, mat, wl.ion_mass, d["em"], d["ep"], d["ph"], d["ion"], wl.dt, wl.seed, 1,
                 mask=pcc.BREMS | pcc.GROUP_EM, precision=pcc.FP64_PLAIN)
@@ -123,7 +124,7 @@ def test_launch_count(pcc, ctx):
     ctx.steps_launch()
     ctx.steps_launch()
     torch.cuda.synchronize()
-    assert pcc.launch_count() - c0 == 2 * 2 * (21 + 3)
+    assert pcc.launch_count() - c0 == 2 * 2 * (15 + 3)
     ctx.read_status()
 
 
