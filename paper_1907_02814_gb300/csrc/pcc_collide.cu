@@ -416,9 +416,11 @@ __device__ __noinline__ EventResult bh_event(const StepArgs* ap, Tab<Real> tb, i
 }
 
 // ---- one electron/positron - ion pair: Brems then Trident -------------------
+// The weights (projectile *wp, target ion.w) are read only for accepted
+// pairs; no event writes a live particle's weight.
 template <typename Real>
 __device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb, int group, int cell, int mat, Real Zf,
-                                        Real coef, float u[3], float wp, float xpos, int t_slot, uint32_t j, Real UB,
+                                        Real coef, float u[3], const float* wp, float xpos, int t_slot, uint32_t j, Real UB,
                                         Real UT, Acc& acc, float& rad, float& wcre, bool& had)
 {
     const StepArgs& a = *ap;
@@ -436,7 +438,7 @@ __device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb,
         if (sig > (Real)0 && UB < x && UB < -expm1(-x)) {
             const int ch = group == kGroupEm ? kChBremsEm : kChBremsEp;
             acc.accepted[ch]++;
-            const EventResult r = brems_event<Real>(ap, tb, group, cell, mat, j, wp, ion.w[t_slot], xpos, f);
+            const EventResult r = brems_event<Real>(ap, tb, group, cell, mat, j, *wp, ion.w[t_slot], xpos, f);
             if (r.created) {
                 acc.created[ch]++;
                 acc.dE += r.dE;
@@ -459,7 +461,7 @@ __device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb,
         if (sig > (Real)0 && UT < x && UT < -expm1(-x)) {
             const int ch = group == kGroupEm ? kChTriEm : kChTriEp;
             acc.accepted[ch]++;
-            const EventResult r = trident_event<Real>(ap, tb, group, cell, j, wp, ion.w[t_slot], xpos, f);
+            const EventResult r = trident_event<Real>(ap, tb, group, cell, j, *wp, ion.w[t_slot], xpos, f);
             if (r.created) {
                 acc.created[ch]++;
                 acc.dE += r.dE;
@@ -566,7 +568,7 @@ __device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
                 const Real UB = u01<Real>(ac.v[2 * h]), UT = u01<Real>(ac.v[2 * h + 1]);
                 if (!quick || UB < bB || UT < bT) {
                     if (quick) acc.candidates[group]++;
-                    ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, w, xp, t0 + (int)(j % Nt), j, UB, UT, acc,
+                    ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, &w, xp, t0 + (int)(j % Nt), j, UB, UT, acc,
                                   rad, wcre, dirty);
                 }
             } else {
@@ -575,7 +577,7 @@ __device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
                     const Real UB = u01<Real>(am.v[2 * h]), UT = u01<Real>(am.v[2 * h + 1]);
                     if (quick && !(UB < bB || UT < bT)) continue;
                     acc.candidates[group]++;
-                    ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, w, xp, t0 + (int)pr.target_of_pair(j), j,
+                    ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, &w, xp, t0 + (int)pr.target_of_pair(j), j,
                                   UB, UT, acc, rad, wcre, dirty);
                 }
             }
@@ -1471,7 +1473,7 @@ __global__ void __launch_bounds__(kBatchedThreads, 4) flat_cand_kernel(const __g
         } else {
             float u[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
             const float xp = P.x ? P.x[sl] : 0.f;
-            ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w[sl], xp, ts, j, u01<float>(r1),
+            ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w + sl, xp, ts, j, u01<float>(r1),
                            u01<float>(r2), acc, rad, wcre, event);
             if (event) {
                 P.ux[sl] = u[0]; P.uy[sl] = u[1]; P.uz[sl] = u[2];
@@ -1543,7 +1545,7 @@ __global__ void __launch_bounds__(kBatchedThreads, 2) caseb_cand_kernel(const __
                 } else {
                     float u[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
                     const float xp = P.x ? P.x[sl] : 0.f;
-                    ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w[sl], xp, ts, j,
+                    ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w + sl, xp, ts, j,
                                    u01<float>(r1), u01<float>(r2), acc, rad, wcre, event);
                     if (event) {
                         P.ux[sl] = u[0]; P.uy[sl] = u[1]; P.uz[sl] = u[2];
