@@ -42,7 +42,7 @@ class Material(C.Structure):
 class Screening(C.Structure):
     _fields_ = [("Z", C.c_int), ("Zstar", C.c_double), ("LTF", C.c_double), ("LD", C.c_double),
                 ("etaTF", C.c_double), ("etaD", C.c_double), ("ITFD", C.c_double), ("LR", C.c_double),
-                ("fC", C.c_double), ("lambdaD", C.c_double), ("ri", C.c_double)]
+                ("fC", C.c_double), ("lambdaD", C.c_double), ("ri", C.c_double), ("tfd_quad", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -51,7 +51,7 @@ class Screening(C.Structure):
 class TableSpec(C.Structure):
     _fields_ = [("n_rows", C.c_int), ("n_cols", C.c_int), ("quad_nodes", C.c_int),
                 ("T_min", C.c_double), ("T_max", C.c_double), ("x_min", C.c_double),
-                ("tri_y_min", C.c_double), ("nr_qbounds", C.c_int)]
+                ("tri_y_min", C.c_double), ("nr_qbounds", C.c_int), ("screening", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -87,6 +87,7 @@ def lib():
             for name in ("orc_I1_yukawa", "orc_I2_yukawa"):
                 getattr(L, name).restype = d; getattr(L, name).argtypes = [d, d]
             L.orc_I_tfd.restype = d; L.orc_I_tfd.argtypes = [d, d, d, d]
+            L.orc_I12_tfd_quad.argtypes = [C.POINTER(Screening), d, _dp, _dp]
             L.orc_dsdk_brems.restype = d; L.orc_dsdk_brems.argtypes = [C.POINTER(Screening), d, d, C.c_int]
             L.orc_dsdk_brems_nr.restype = d; L.orc_dsdk_brems_nr.argtypes = [C.POINTER(Screening), d, d, C.c_int]
             L.orc_dsdk_brems_rel.restype = d; L.orc_dsdk_brems_rel.argtypes = [C.POINTER(Screening), d, d, d]
@@ -121,6 +122,7 @@ def lib():
 # ---------------------------------------------------------------- physics --
 TB_BREMS, TB_BH, TB_TRI_GP, TB_TRI_SPLIT = 0, 1, 2, 3
 NR_EXACT, NR_PRINTED = 0, 1
+SCREEN_REDUCED, SCREEN_TFD_QUAD = 0, 1
 PROC_BREMS, PROC_TRIDENT, PROC_BH = 1, 2, 4
 
 
@@ -152,6 +154,21 @@ def I2(delta, L):
 
 def I_tfd(etaTF, LTF, etaD, LD):
     return lib().orc_I_tfd(float(etaTF), float(LTF), float(etaD), float(LD))
+
+
+def I12_tfd_quad(scr, delta):
+    """(I1, I2) of Eqs. (defphi1), (defphi2) for the full TFD potential."""
+    a, b = C.c_double(), C.c_double()
+    lib().orc_I12_tfd_quad(C.byref(scr), float(delta), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def screening_tfd(mat: Material) -> Screening:
+    """Screening of a material whose relativistic Brems and BH cross sections
+    use the full TFD potential (I1, I2 by quadrature) instead of L_R."""
+    s = screening(mat)
+    s.tfd_quad = 1
+    return s
 
 
 def dsdk_brems(scr, gamma1, k, qb=NR_EXACT):
@@ -190,9 +207,9 @@ def gauss_legendre(n):
 
 # ----------------------------------------------------------------- tables --
 def table_spec(n_rows=256, n_cols=256, quad_nodes=8, gamma_min=1.002, gamma_max=2000.0,
-               cutoff_exp=7, tri_y_min=1e-5, nr_qbounds=NR_EXACT) -> TableSpec:
+               cutoff_exp=7, tri_y_min=1e-5, nr_qbounds=NR_EXACT, screening=SCREEN_REDUCED) -> TableSpec:
     return TableSpec(n_rows, n_cols, quad_nodes, gamma_min - 1.0, gamma_max - 1.0,
-                     10.0 ** (-cutoff_exp), tri_y_min, nr_qbounds)
+                     10.0 ** (-cutoff_exp), tri_y_min, nr_qbounds, screening)
 
 
 class OracleTables:

@@ -174,6 +174,65 @@ double orc_I2_yukawa(double d, double L)
     return 0.5 * two_I2;
 }
 
+/* Eq. (defF) for the potential of Eq. (V_TFD): the Fourier transform of each
+ * Yukawa term (q_i/r) exp(-r/L_i) gives 1 - F = (L_i u)^2 / (1 + (L_i u)^2)
+ * for its charge fraction, so 1 - F(u) is their sum weighted by
+ * eta_i = q_i/q (u in units of m_e c, lengths in units of r_C). */
+static double one_minus_F_tfd(const orc_screening *s, double u)
+{
+    double a = s->LTF * u, b = s->LD * u;
+    return s->etaTF * a * a / (1.0 + a * a) + s->etaD * b * b / (1.0 + b * b);
+}
+
+/* Eqs. (defphi1) and (defphi2) with the form factor of the full
+ * Thomas-Fermi-Debye potential, by quadrature in t = ln u over
+ * [ln delta, 0]: composite 8-point Gauss-Legendre on equal panels no wider
+ * than 1/2 (the form factor changes over about one unit of ln u around
+ * u = 1/L_TF and u = 1/L_D).  With r = u/delta the integrands are
+ *   I1: (u - delta)^2 / u^3 du = (1 - 1/r)^2 dt,
+ *   I2: [u^3 - 6 delta^2 u ln(u/delta) + 3 delta^2 u - 4 delta^3] / u^4 du
+ *       = (1 + (3 - 6 ln r)/r^2 - 4/r^3) dt,
+ * each times (1 - F(u))^2.  Zero for delta >= 1 (empty range). */
+void orc_I12_tfd_quad(const orc_screening *s, double delta, double *I1, double *I2)
+{
+    double gx[8], gw[8];
+    orc_gauss_legendre(8, gx, gw);
+    *I1 = 0.0;
+    *I2 = 0.0;
+    if (!(delta > 0.0 && delta < 1.0)) return;
+    double t0 = log(delta);
+    int n = (int)ceil(-t0 / 0.5);
+    double h = -t0 / n;
+    double s1 = 0.0, s2 = 0.0;
+    for (int p = 0; p < n; ++p) {
+        double mid = t0 + (p + 0.5) * h;
+        for (int q = 0; q < 8; ++q) {
+            double t = mid + 0.5 * h * gx[q];
+            double lr = t - t0;                 /* ln r */
+            double r = exp(lr);
+            double f = one_minus_F_tfd(s, exp(t));
+            double f2 = f * f;
+            double a = -expm1(-lr);             /* 1 - 1/r */
+            s1 += gw[q] * a * a * f2;
+            s2 += gw[q] * (1.0 + (3.0 - 6.0 * lr) / (r * r) - 4.0 / (r * r * r)) * f2;
+        }
+    }
+    *I1 = 0.5 * h * s1;
+    *I2 = 0.5 * h * s2;
+}
+
+/* I1, I2 of the material's screening mode: the reduced single-Yukawa
+ * potential at L_R (Sec. II.B.2), or the full TFD potential by quadrature. */
+static void screening_I12(const orc_screening *s, double delta, double *I1, double *I2)
+{
+    if (s->tfd_quad) {
+        orc_I12_tfd_quad(s, delta, I1, I2);
+    } else {
+        *I1 = orc_I1_yukawa(delta, s->LR);
+        *I2 = orc_I2_yukawa(delta, s->LR);
+    }
+}
+
 /* g(dp+, dp-, eta, L) of Eq. (cs_br_nr). */
 static double g_nr(double dpp, double dpm, double eta, double L)
 {
@@ -224,13 +283,15 @@ double orc_dsdk_brems_nr(const orc_screening *s, double gamma1, double k, int nr
 }
 
 /* Eq. (csre) (fc = 0) and Eq. (csur) (fc = f_C): relativistic Brems with the
- * reduced single-Yukawa screening functions at L = L_R. */
+ * screening functions of the material's mode (reduced single Yukawa at
+ * L = L_R, or the full TFD potential by quadrature). */
 double orc_dsdk_brems_rel(const orc_screening *s, double gamma1, double k, double fc)
 {
     if (!(k > 0.0 && k < gamma1 - 1.0)) return 0.0;
     double eps = (gamma1 - k) / gamma1;
     double delta = k / (2.0 * gamma1 * (gamma1 - k));
-    double I1 = orc_I1_yukawa(delta, s->LR), I2 = orc_I2_yukawa(delta, s->LR);
+    double I1, I2;
+    screening_I12(s, delta, &I1, &I2);
     double Z = s->Z;
     double v = 4.0 * Z * Z * R_E * R_E * ALPHA / k
              * ((1.0 + eps * eps) * (I1 + 1.0 - fc) - 2.0 / 3.0 * eps * (I2 + 5.0 / 6.0 - fc));
@@ -255,7 +316,8 @@ double orc_dsdg_bh(const orc_screening *s, double k, double gp)
     double gm = k - gp;
     if (!(gp > 1.0 && gm > 1.0)) return 0.0;
     double delta = k / (2.0 * gp * gm);
-    double I1 = orc_I1_yukawa(delta, s->LR), I2 = orc_I2_yukawa(delta, s->LR);
+    double I1, I2;
+    screening_I12(s, delta, &I1, &I2);
     double Z = s->Z;
     double v = 4.0 * Z * Z * R_E * R_E * ALPHA / (k * k * k)
              * ((gp * gp + gm * gm) * (I1 + 1.0) + 2.0 / 3.0 * gp * gm * (I2 + 5.0 / 6.0));
@@ -454,9 +516,11 @@ int orc_tables_build(orc_tables *t)
     const orc_table_spec *sp = &t->spec;
     int Q = sp->quad_nodes;
     if (Q < 1 || Q > 64 || sp->n_rows < 2 || sp->n_cols < 2) return 1;
+    if (sp->screening != ORC_SCREEN_REDUCED && sp->screening != ORC_SCREEN_TFD_QUAD) return 1;
     double gx[64], gw[64];
     orc_gauss_legendre(Q, gx, gw);
     size_t R = sp->n_rows, C = sp->n_cols;
+    for (int m = 0; m < t->n_mat; ++m) t->scr[m].tfd_quad = sp->screening == ORC_SCREEN_TFD_QUAD;
     for (int m = 0; m < t->n_mat; ++m) {
         for (int r = 0; r < sp->n_rows; ++r) {
             t->brems_sigma[m * R + r] = build_row(t, TB_BREMS, m, r, t->brems_cdf + (m * R + r) * C, gx, gw);

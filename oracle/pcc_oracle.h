@@ -45,9 +45,12 @@ typedef struct {
     double LR;             /* Eq. (lambert-W)                                */
     double fC;             /* Coulomb correction (Sec. II.B.3)               */
     double lambdaD, ri;    /* unclamped Debye length and ion-sphere radius [m] */
+    int tfd_quad;          /* 1: relativistic Brems and BH use I1, I2 of the full
+                              TFD potential by quadrature; 0: the reduced L_R  */
 } orc_screening;
 
 enum { ORC_NR_EXACT = 0, ORC_NR_PRINTED = 1 };
+enum { ORC_SCREEN_REDUCED = 0, ORC_SCREEN_TFD_QUAD = 1 };
 
 typedef struct {
     int n_rows, n_cols, quad_nodes;
@@ -55,6 +58,7 @@ typedef struct {
     double x_min;          /* Brems cut-off k/(gamma-1) >= x_min (Sec. III.A)      */
     double tri_y_min;      /* Trident pair-energy column floor                     */
     int nr_qbounds;        /* ORC_NR_EXACT or ORC_NR_PRINTED                       */
+    int screening;         /* ORC_SCREEN_REDUCED or ORC_SCREEN_TFD_QUAD            */
 } orc_table_spec;
 
 /* Tables; all arrays owned by the caller.
@@ -63,7 +67,7 @@ typedef struct {
 typedef struct {
     orc_table_spec spec;
     int n_mat;
-    const orc_screening *scr;
+    orc_screening *scr;
     double *brems_sigma, *brems_cdf;
     double *bh_sigma, *bh_cdf;
     double *tri_gp_cdf, *tri_split_cdf;
@@ -95,6 +99,7 @@ double orc_fC(int Z);
 double orc_I1_yukawa(double delta, double L);
 double orc_I2_yukawa(double delta, double L);
 double orc_I_tfd(double etaTF, double LTF, double etaD, double LD);
+void   orc_I12_tfd_quad(const orc_screening *s, double delta, double *I1, double *I2);
 double orc_dsdk_brems(const orc_screening *s, double gamma1, double k, int nr_qbounds);
 double orc_dsdk_brems_nr(const orc_screening *s, double gamma1, double k, int nr_qbounds);
 double orc_dsdk_brems_rel(const orc_screening *s, double gamma1, double k, double fc);
