@@ -76,13 +76,23 @@ typedef struct {
  * split y linear on [0, 1]; Trident pair energy y = (gamma_p-2)/(gamma_1-3)
  * log-spaced on [tri_y_min, 1].  quad_nodes Gauss-Legendre points per
  * column interval.  nr_qbounds 0: momentum-transfer bounds p1 +/- p2;
- * 1: the printed 2 p1 - k and k (Sec. II.B.1). */
+ * 1: the printed 2 p1 - k and k (Sec. II.B.1).  screening: the screening
+ * functions I1, I2 (Eqs. defphi1, defphi2) of the relativistic Brems
+ * regimes (Eqs. csre, csur) and of Bethe-Heitler (Eq. dsdkbh);
+ * PCC_SCREEN_REDUCED takes the closed forms (Eqs. deriv_I1, deriv_I2) of the
+ * reduced single-Yukawa potential at L_R (Eq. lambert-W), as the paper's
+ * code does; PCC_SCREEN_TFD_QUAD integrates them numerically with the form
+ * factor (Eq. defF) of the full Thomas-Fermi-Debye potential (Eq. V_TFD),
+ * the reference the paper compares the reduced formula with (Sec. II.B.2-3,
+ * Sec. II.C).  The non-relativistic regime uses the full potential in both. */
+enum { PCC_SCREEN_REDUCED = 0, PCC_SCREEN_TFD_QUAD = 1 };
 typedef struct {
     int n_rows, n_cols, quad_nodes;
     double gamma_min, gamma_max;
     int cutoff_exp;
     double tri_y_min;
     int nr_qbounds;
+    int screening;          /* PCC_SCREEN_REDUCED or PCC_SCREEN_TFD_QUAD */
 } pcc_table_spec;
 
 /* One species in cell-region layout (all device memory, caller-owned).

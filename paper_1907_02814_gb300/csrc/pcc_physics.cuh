@@ -172,16 +172,25 @@ __device__ inline double dsdk_nonrel(const Screen& s, double g1, double k, int p
     return born * (b1 / b2) * expm1(-a / b1) / expm1(-a / b2);
 }
 
-// Eq. (csre) with fc = 0, Eq. (csur) with fc = f_C.
-__device__ inline double dsdk_relativistic(const Screen& s, double g1, double k, double fc)
+// delta of Eq. (csre): the minimum momentum transfer k / (2 gamma1 gamma2).
+__device__ __forceinline__ double brems_delta(double g1, double k) { return k / (2.0 * g1 * (g1 - k)); }
+
+// Eq. (csre) with fc = 0, Eq. (csur) with fc = f_C, for the screening
+// functions I1, I2 at delta = brems_delta(g1, k).
+__device__ inline double dsdk_relativistic_I(const Screen& s, double g1, double k, double fc, double I1, double I2)
 {
     if (!(k > 0.0 && k < g1 - 1.0)) return 0.0;
     const double eps = (g1 - k) / g1;
-    const double d = k / (2.0 * g1 * (g1 - k));
-    const double I1 = yukawa_I1(d, s.LR), I2 = yukawa_I2(d, s.LR);
     const double v = 4.0 * s.Z * s.Z * kRe * kRe * kAlpha / k *
                      ((1.0 + eps * eps) * (I1 + 1.0 - fc) - (2.0 / 3.0) * eps * (I2 + 5.0 / 6.0 - fc));
     return fmax(v, 0.0);
+}
+
+// The same with the reduced single-Yukawa potential at L = L_R.
+__device__ inline double dsdk_relativistic(const Screen& s, double g1, double k, double fc)
+{
+    const double d = brems_delta(g1, k);
+    return dsdk_relativistic_I(s, g1, k, fc, yukawa_I1(d, s.LR), yukawa_I2(d, s.LR));
 }
 
 __device__ __forceinline__ double dsdk_brems(const Screen& s, double g1, double k, int printed)
@@ -192,16 +201,21 @@ __device__ __forceinline__ double dsdk_brems(const Screen& s, double g1, double 
 
 // ---- Sec. II.C-D -----------------------------------------------------------
 
-// Eq. (dsdkbh).
-__device__ inline double dsdg_bethe_heitler(const Screen& s, double k, double gp)
+// Eq. (dsdkbh) for the screening functions I1, I2 at delta = k / (2 gamma+ gamma-).
+__device__ inline double dsdg_bethe_heitler_I(const Screen& s, double k, double gp, double I1, double I2)
 {
     const double gm = k - gp;
     if (!(gp > 1.0 && gm > 1.0)) return 0.0;
-    const double d = k / (2.0 * gp * gm);
-    const double I1 = yukawa_I1(d, s.LR), I2 = yukawa_I2(d, s.LR);
     const double v = 4.0 * s.Z * s.Z * kRe * kRe * kAlpha / (k * k * k) *
                      ((gp * gp + gm * gm) * (I1 + 1.0) + (2.0 / 3.0) * gp * gm * (I2 + 5.0 / 6.0));
     return fmax(v, 0.0);
+}
+
+// The same with the reduced single-Yukawa potential at L = L_R.
+__device__ inline double dsdg_bethe_heitler(const Screen& s, double k, double gp)
+{
+    const double d = k / (2.0 * gp * (k - gp));
+    return dsdg_bethe_heitler_I(s, k, gp, yukawa_I1(d, s.LR), yukawa_I2(d, s.LR));
 }
 
 // Gryaznykh fit of the total Trident cross section, zero below gamma1 = 3.

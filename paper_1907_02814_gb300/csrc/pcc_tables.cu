@@ -63,14 +63,68 @@ __device__ void legendre_nodes(int n, double* x, double* w)
     }
 }
 
+// Flags of the table kernels: the printed non-relativistic momentum-transfer
+// bounds, and the TFD-quadrature screening mode.
+constexpr int kFlagPrinted = 1, kFlagTfdQuad = 2;
+constexpr int kTfdNodes = 12;
+
+// Eqs. (defphi1) and (defphi2) for the full Thomas-Fermi-Debye potential,
+// whose form factor (Eq. defF, Eq. V_TFD) is
+//   1 - F(u) = eta_TF a^2 / (1 + a^2) + eta_D b^2 / (1 + b^2),  a = L_TF u, b = L_D u,
+// by quadrature in t = ln u on unit panels from t = 0 down to ln delta (the
+// last one shorter), kTfdNodes-point Gauss-Legendre each (nodes gx, gw on
+// [-1, 1]).  With r = u/delta the integrands in t are (1 - 1/r)^2 (1 - F)^2
+// and (1 + (3 - 6 ln r)/r^2 - 4/r^3) (1 - F)^2.  Zero for delta >= 1.
+__device__ void tfd_I12(const Screen& s, double d, const double* gx, const double* gw, double& I1, double& I2)
+{
+    I1 = 0.0;
+    I2 = 0.0;
+    if (!(d > 0.0 && d < 1.0)) return;
+    const double t0 = log(d);
+    for (double hi = 0.0; hi > t0; hi -= 1.0) {
+        const double lo = fmax(hi - 1.0, t0);
+        const double h = 0.5 * (hi - lo), m = 0.5 * (hi + lo);
+        double p1 = 0.0, p2 = 0.0;
+        for (int q = 0; q < kTfdNodes; ++q) {
+            const double t = m + h * gx[q];
+            const double lr = t - t0, ir = exp(-lr);
+            const double u = exp(t);
+            const double a2 = s.LTF * s.LTF * u * u, b2 = s.LD * s.LD * u * u;
+            const double f = s.etaTF * a2 / (1.0 + a2) + s.etaD * b2 / (1.0 + b2);
+            const double f2 = f * f;
+            const double om = -expm1(-lr);
+            p1 += gw[q] * om * om * f2;
+            p2 += gw[q] * (1.0 + (3.0 - 6.0 * lr) * ir * ir - 4.0 * ir * ir * ir) * f2;
+        }
+        I1 += h * p1;
+        I2 += h * p2;
+    }
+}
+
 template <int KIND>
-__device__ __forceinline__ double integrand(const Screen& s, double rowv, double v, int printed)
+__device__ __forceinline__ double integrand(const Screen& s, double rowv, double v, int flags, const double* tx,
+                                            const double* tw)
 {
     if (KIND == kBrems) {
         const double x = exp(v);
-        return dsdk_brems(s, 1.0 + rowv, x * rowv, printed) * rowv * x;
+        const double g1 = 1.0 + rowv, k = x * rowv;
+        if ((flags & kFlagTfdQuad) && g1 > 2.0) {
+            if (!(k > 0.0 && k < g1 - 1.0)) return 0.0;
+            double I1, I2;
+            tfd_I12(s, brems_delta(g1, k), tx, tw, I1, I2);
+            return dsdk_relativistic_I(s, g1, k, g1 <= 100.0 ? 0.0 : s.fC, I1, I2) * rowv * x;
+        }
+        return dsdk_brems(s, g1, k, flags & kFlagPrinted) * rowv * x;
     } else if (KIND == kBH) {
-        return dsdg_bethe_heitler(s, 2.0 + rowv, 1.0 + v * rowv) * rowv;
+        const double k = 2.0 + rowv, gp = 1.0 + v * rowv;
+        if (flags & kFlagTfdQuad) {
+            const double gm = k - gp;
+            if (!(gp > 1.0 && gm > 1.0)) return 0.0;
+            double I1, I2;
+            tfd_I12(s, k / (2.0 * gp * gm), tx, tw, I1, I2);
+            return dsdg_bethe_heitler_I(s, k, gp, I1, I2) * rowv;
+        }
+        return dsdg_bethe_heitler(s, k, gp) * rowv;
     } else if (KIND == kTriPair) {
         const double y = exp(v);
         return trident_pair_shape(3.0 + rowv, 2.0 + y * rowv) * rowv * y;
@@ -81,25 +135,26 @@ __device__ __forceinline__ double integrand(const Screen& s, double rowv, double
 
 template <int KIND>
 __device__ double panel(const Screen& s, double rowv, double a, double b, int Q, const double* gx, const double* gw,
-                        int printed)
+                        int flags, const double* tx, const double* tw)
 {
     const double h = 0.5 * (b - a), m = 0.5 * (a + b);
     double acc = 0.0;
-    for (int q = 0; q < Q; ++q) acc += gw[q] * integrand<KIND>(s, rowv, m + h * gx[q], printed);
+    for (int q = 0; q < Q; ++q) acc += gw[q] * integrand<KIND>(s, rowv, m + h * gx[q], flags, tx, tw);
     return h * acc;
 }
 
 // One block per (row, material): integrals over every column interval, then
 // the cumulative sum in column order, normalisation and the total.
 template <int KIND>
-__global__ void table_rows_kernel(const double* screen, TableGeom g, int Q, int printed, double* sigma_out,
+__global__ void table_rows_kernel(const double* screen, TableGeom g, int Q, int flags, double* sigma_out,
                                   double* cdf_out)
 {
     extern __shared__ double part[];   // [n_cols]
-    __shared__ double gx[kMaxQuad], gw[kMaxQuad];
+    __shared__ double gx[kMaxQuad], gw[kMaxQuad], tx[kTfdNodes], tw[kTfdNodes];
     __shared__ double total;
     const int r = blockIdx.x, mat = blockIdx.y, nc = g.n_cols;
     if (threadIdx.x == 0) legendre_nodes(Q, gx, gw);
+    if (threadIdx.x == 32 && (flags & kFlagTfdQuad)) legendre_nodes(kTfdNodes, tx, tw);
     Screen s{};
     if (KIND == kBrems || KIND == kBH) s = load_screen(screen + (size_t)mat * kScreenFields);
     const double rowv = g.T_min * pow(g.T_max / g.T_min, (double)r / (g.n_rows - 1));
@@ -123,21 +178,21 @@ __global__ void table_rows_kernel(const double* screen, TableGeom g, int Q, int 
             for (int i = 0; i < kEdgePanels; ++i) {
                 f *= 0.25;
                 const double hi = b - (b - a) * f;
-                v += panel<KIND>(s, rowv, lo, hi, Q, gx, gw, printed);
+                v += panel<KIND>(s, rowv, lo, hi, Q, gx, gw, flags, tx, tw);
                 lo = hi;
             }
-            v += panel<KIND>(s, rowv, lo, b, Q, gx, gw, printed);
+            v += panel<KIND>(s, rowv, lo, b, Q, gx, gw, flags, tx, tw);
         } else if (left) {
             double hi = b, f = 1.0;
             for (int i = 0; i < kEdgePanels; ++i) {
                 f *= 0.25;
                 const double lo = a + (b - a) * f;
-                v += panel<KIND>(s, rowv, lo, hi, Q, gx, gw, printed);
+                v += panel<KIND>(s, rowv, lo, hi, Q, gx, gw, flags, tx, tw);
                 hi = lo;
             }
-            v += panel<KIND>(s, rowv, a, hi, Q, gx, gw, printed);
+            v += panel<KIND>(s, rowv, a, hi, Q, gx, gw, flags, tx, tw);
         } else {
-            v = panel<KIND>(s, rowv, a, b, Q, gx, gw, printed);
+            v = panel<KIND>(s, rowv, a, b, Q, gx, gw, flags, tx, tw);
         }
         part[c + 1] = v;
     }
@@ -236,7 +291,8 @@ extern "C" int pcc_tables_build(pcc_ctx* ctx, const pcc_material* mats, int n_ma
     if (n_mats < 1 || n_mats > 4096 || s.n_rows < 2 || s.n_rows > 4096 || s.n_cols < 3 || s.n_cols > 4096 ||
         s.quad_nodes < 1 || s.quad_nodes > kMaxQuad || !(s.gamma_min > 1.0) || !(s.gamma_max > s.gamma_min) ||
         s.cutoff_exp < 1 || s.cutoff_exp > 30 || !(s.tri_y_min > 0.0 && s.tri_y_min < 1.0) ||
-        (s.nr_qbounds != 0 && s.nr_qbounds != 1)) {
+        (s.nr_qbounds != 0 && s.nr_qbounds != 1) ||
+        (s.screening != PCC_SCREEN_REDUCED && s.screening != PCC_SCREEN_TFD_QUAD)) {
         set_error("pcc_tables_build: invalid table spec");
         return PCC_E_INVALID;
     }
@@ -277,6 +333,7 @@ extern "C" int pcc_tables_build(pcc_ctx* ctx, const pcc_material* mats, int n_ma
     material_prep_kernel<<<(n_mats + 63) / 64, 64, 0, st>>>(dmats, n_mats, ctx->screen);
 
     const TableGeom g = make_geom(s);
+    const int flags = (s.nr_qbounds ? kFlagPrinted : 0) | (s.screening == PCC_SCREEN_TFD_QUAD ? kFlagTfdQuad : 0);
     const size_t smem = C * sizeof(double);
     if (smem > 48 * 1024) {
         cudaFuncSetAttribute(table_rows_kernel<kBrems>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -284,13 +341,13 @@ extern "C" int pcc_tables_build(pcc_ctx* ctx, const pcc_material* mats, int n_ma
         cudaFuncSetAttribute(table_rows_kernel<kTriPair>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(table_rows_kernel<kTriSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    table_rows_kernel<kBrems><<<dim3(s.n_rows, n_mats), 128, smem, st>>>(ctx->screen, g, s.quad_nodes, s.nr_qbounds,
+    table_rows_kernel<kBrems><<<dim3(s.n_rows, n_mats), 128, smem, st>>>(ctx->screen, g, s.quad_nodes, flags,
                                                                          ctx->brems_sigma, ctx->brems_cdf);
-    table_rows_kernel<kBH><<<dim3(s.n_rows, n_mats), 128, smem, st>>>(ctx->screen, g, s.quad_nodes, s.nr_qbounds,
+    table_rows_kernel<kBH><<<dim3(s.n_rows, n_mats), 128, smem, st>>>(ctx->screen, g, s.quad_nodes, flags,
                                                                       ctx->bh_sigma, ctx->bh_cdf);
-    table_rows_kernel<kTriPair><<<dim3(s.n_rows, 1), 128, smem, st>>>(ctx->screen, g, s.quad_nodes, s.nr_qbounds,
+    table_rows_kernel<kTriPair><<<dim3(s.n_rows, 1), 128, smem, st>>>(ctx->screen, g, s.quad_nodes, flags,
                                                                       nullptr, ctx->tri_gp_cdf);
-    table_rows_kernel<kTriSplit><<<dim3(s.n_rows, 1), 128, smem, st>>>(ctx->screen, g, s.quad_nodes, s.nr_qbounds,
+    table_rows_kernel<kTriSplit><<<dim3(s.n_rows, 1), 128, smem, st>>>(ctx->screen, g, s.quad_nodes, flags,
                                                                        nullptr, ctx->tri_split_cdf);
     auto conv = [&](const double* in, float* out, size_t n, int lg) {
         to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n, lg);

@@ -34,7 +34,7 @@ class Material(C.Structure):
 class TableSpec(C.Structure):
     _fields_ = [("n_rows", C.c_int), ("n_cols", C.c_int), ("quad_nodes", C.c_int), ("gamma_min", C.c_double),
                 ("gamma_max", C.c_double), ("cutoff_exp", C.c_int), ("tri_y_min", C.c_double),
-                ("nr_qbounds", C.c_int)]
+                ("nr_qbounds", C.c_int), ("screening", C.c_int)]
 
 
 class Species(C.Structure):
@@ -132,9 +132,13 @@ def material(Z, Zstar, n_i, T_e, s_TF=1.0, s_D=1.0) -> Material:
     return Material(int(Z), float(Zstar), float(n_i), float(T_e), float(s_TF), float(s_D))
 
 
+SCREEN_REDUCED, SCREEN_TFD_QUAD = 0, 1
+
+
 def table_spec(n_rows=256, n_cols=256, quad_nodes=8, gamma_min=1.002, gamma_max=2000.0, cutoff_exp=7,
-               tri_y_min=1e-5, nr_qbounds=0) -> TableSpec:
-    return TableSpec(n_rows, n_cols, quad_nodes, gamma_min, gamma_max, cutoff_exp, tri_y_min, nr_qbounds)
+               tri_y_min=1e-5, nr_qbounds=0, screening=SCREEN_REDUCED) -> TableSpec:
+    return TableSpec(n_rows, n_cols, quad_nodes, gamma_min, gamma_max, cutoff_exp, tri_y_min, nr_qbounds,
+                     screening)
 
 
 class Context:
