@@ -167,6 +167,27 @@ def thin_target_beam(ratio, n_cells=16, e_per_cell=64, seed=1, dt=1e-15, gamma=N
     return wl
 
 
+def thin_target_photon_beam(ratio, k_mev=100.0, n_cells=16, g_per_cell=64, seed=1, dt=1e-15):
+    """Mono-energetic photon beam (k_mev along +x) through neutral Cu at rest,
+    the Bethe-Heitler counterpart of Fig. valid_brem_tf: n_gamma = 1e27 m^-3,
+    n_i = 8e28 m^-3 with W_i / W_gamma = ``ratio``."""
+    k = k_mev / MEC2_MEV
+    n_g, n_i = 1e27, 8e28
+    w_g = n_g / g_per_cell
+    i_per_cell = int(round(n_i / (ratio * w_g)))
+    cell_g = np.repeat(np.arange(n_cells), g_per_cell)
+    cell_i = np.repeat(np.arange(n_cells), i_per_cell)
+    ph = _species(np.full(len(cell_g), k), np.zeros(len(cell_g)), np.zeros(len(cell_g)),
+                  np.full(len(cell_g), w_g), cell_g)
+    ion = _species(np.zeros(len(cell_i)), np.zeros(len(cell_i)), np.zeros(len(cell_i)),
+                   np.full(len(cell_i), n_i / i_per_cell), cell_i)
+    mat = Material(29, 0.0, n_i, 0.0)
+    wl = Workload(f"thin_target_photons_ratio{ratio}", n_cells, [mat], np.zeros(n_cells, np.int32), MASS_CU, dt,
+                  seed, 1)
+    wl.species = {"em": empty_species(), "ep": empty_species(), "ph": ph, "ion": ion}
+    return wl
+
+
 def au_foil(n_cells=16384, mean_e=256, i_per_cell=64, seed=2, dt=1e-15, dx=2.4e-9):
     """1D Au foil: Poisson(mean_e) electrons per cell, kinetic energy ~ E^-2 on
     0.1-100 MeV, isotropic, weights log-uniform over three decades with mean

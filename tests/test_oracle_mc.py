@@ -1,6 +1,7 @@
 """Pins of the oracle's tables, pairing and Monte Carlo step (Sec. III.A)
 against quadrature, brute force and the paper's analytic thin-target yield
-(Eq. N_br_theo1/2, Fig. valid_brem_tf)."""
+(Eq. N_br_theo1/2, Fig. valid_brem_tf), and the same thin-target check for
+Bethe-Heitler and Trident pair creation."""
 import math
 
 import numpy as np
@@ -174,6 +175,64 @@ def test_thin_target_yield_independent_of_weight_ratio(orc):
     exp_counts = probs / probs.sum() * obs.sum()
     chi2 = ((obs - exp_counts) ** 2 / exp_counts).sum()
     assert stats.chi2.sf(chi2, len(obs) - 1) > 0.01
+
+
+@pytest.mark.slow
+def test_thin_target_bh_yield_independent_of_weight_ratio(orc):
+    """The Bethe-Heitler counterpart of Fig. valid_brem_tf: a 100 MeV photon
+    beam in neutral Cu (n_gamma = 1e21 cm^-3, n_i = 8e22 cm^-3) converts
+    n_gamma (1 - (1 - q)^S) photons into pairs in S steps, q = n_i c
+    sigma_BH dt (a converted photon is absorbed), whatever W_i/W_gamma in
+    {2, 1, 1/2}; the positron energies follow dsigma_BH/dgamma_+ (Eq. dsdkbh)."""
+    k = 100.0 / 0.51099895
+    steps, dt, n_cells = 8, 4e-13, 256
+    yields, spectra = {}, {}
+    for ratio in (2.0, 1.0, 0.5):
+        wl = W.thin_target_photon_beam(ratio, n_cells=n_cells, g_per_cell=64, seed=13, dt=dt)
+        T, sp, ledger, st = _run(orc, wl, steps, orc.PROC_BH)
+        ep, em = sp["ep"].as_dict(), sp["em"].as_dict()
+        assert len(ep["w"]) == len(em["w"])
+        yields[ratio] = (ep["w"].astype(float).sum(), len(ep["w"]))
+        spectra[ratio] = np.sqrt(1.0 + ep["ux"].astype(float) ** 2 + ep["uy"] ** 2 + ep["uz"] ** 2)
+    s = T.screening(0)
+    sigma = quad(lambda gp: orc.dsdg_bh(s, k, gp), 1.0, k - 1.0)
+    q = 8e28 * C_LIGHT * sigma * dt
+    expected = 1e27 * (1.0 - (1.0 - q) ** steps) * n_cells        # sum of positron weights over cells
+    for ratio, (wsum, count) in yields.items():
+        print(f"\n[thin target BH] W_i/W_g = {ratio}: yield / theory = {wsum / expected:.4f} ({count} pairs)")
+        assert count > 300
+        assert abs(wsum / expected - 1) < 4 / math.sqrt(count) + 0.01, (ratio, wsum / expected, count)
+    gp = np.concatenate(list(spectra.values()))
+    edges = np.linspace(1.0, k - 1.0, 9)
+    obs = np.histogram(gp, edges)[0]
+    probs = np.array([quad(lambda g: orc.dsdg_bh(s, k, g), a, b) for a, b in zip(edges[:-1], edges[1:])]) / sigma
+    exp_counts = probs / probs.sum() * obs.sum()
+    chi2 = ((obs - exp_counts) ** 2 / exp_counts).sum()
+    assert stats.chi2.sf(chi2, len(obs) - 1) > 0.01
+
+
+@pytest.mark.slow
+def test_thin_target_trident_yield_independent_of_weight_ratio(orc):
+    """Coulomb Trident in the same thin target: a 500 MeV electron beam
+    creates n_e n_i v sigma_T t pairs per unit volume (Gryaznykh fit of
+    Sec. II.D), whatever W_i/W_e in {2, 1, 1/2}.  One step: the pairs created
+    in a step become projectiles only after it, so a single step counts no
+    cascade of secondary Tridents (which several steps would add at second
+    order), and a recoiled electron's later pairs change sigma_T only at
+    second order in its ~4 % conversion probability."""
+    g = 1.0 + 500.0 / 0.51099895
+    v = C_LIGHT * math.sqrt(1.0 - 1.0 / g ** 2)
+    steps, dt, n_cells = 1, 3.2e-11, 256
+    sigma = orc.sigma_trident(29, g)
+    expected = 1e27 * 8e28 * v * sigma * steps * dt * n_cells
+    for ratio in (2.0, 1.0, 0.5):
+        wl = W.thin_target_beam(ratio, n_cells=n_cells, e_per_cell=64, seed=14, dt=dt, gamma=g)
+        T, sp, ledger, st = _run(orc, wl, steps, orc.PROC_TRIDENT)
+        ep = sp["ep"].as_dict()
+        wsum, count = ep["w"].astype(float).sum(), len(ep["w"])
+        print(f"\n[thin target Trident] W_i/W_e = {ratio}: yield / theory = {wsum / expected:.4f} ({count} pairs)")
+        assert count > 300
+        assert abs(wsum / expected - 1) < 4 / math.sqrt(count) + 0.015, (ratio, wsum / expected, count)
 
 
 @pytest.mark.slow
