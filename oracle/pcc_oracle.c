@@ -695,7 +695,7 @@ uint32_t orc_perm_elem(uint32_t j, uint32_t n, const uint32_t rk[4])
 /* ------------------------------------------------------------------------ */
 
 enum { G_EM = 0, G_EP = 1, G_BH = 2 };
-enum { PU_PERM = 0, PU_ACCEPT = 1, PU_EVT_B = 2, PU_EVT_T1 = 3, PU_EVT_T2 = 4, PU_EVT_BH = 5 };
+enum { PU_PERM = 0, PU_ACCEPT = 1, PU_EVT_B = 2, PU_EVT_T1 = 3, PU_EVT_T2 = 4, PU_EVT_BH = 5, PU_ACCEPT_EXT = 6 };
 enum { CH_BREMS_EM = 0, CH_BREMS_EP = 1, CH_TRI_EM = 2, CH_TRI_EP = 3, CH_BH = 4 };
 
 static uint32_t tag(int group, int purpose, uint32_t m) { return (uint32_t)group | ((uint32_t)purpose << 4) | (m << 8); }
@@ -705,6 +705,34 @@ static void philox_at(uint32_t c0, uint32_t cell, uint64_t step, uint32_t tg, ui
     uint32_t ctr[4] = { c0, cell, (uint32_t)step, tg };
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
     orc_philox4x32_10(ctr, key, out);
+}
+
+/* Where the second word of an accept uniform comes from: word w of the draw
+ * (c0, cell, step, tag) with the ACCEPT_EXT purpose. */
+typedef struct { uint32_t c0, cell; uint64_t step; uint32_t tag; uint64_t seed; int w; } accept_src;
+
+/* The accept decision U < p (Eq. proba3: the pair collides with probability
+ * p = 1 - exp(-x)) for the uniform U = (2^32 r + r' + 1/2) 2^-64, compared
+ * digit by digit: the first word r settles it unless r = floor(2^32 p), and
+ * only then is the second word r' drawn.  Every p in [0, 1] is honoured
+ * down to 2^-64, which per-pair probabilities of rare processes at small
+ * time steps need (Trident: ~1e-10 per pair at the paper's 7.4e-3 fs). */
+static int accept_u(uint32_t r, double p, const accept_src *src)
+{
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return 1;
+    double X = ldexp(p, 32), fl = floor(X);
+    if ((double)r < fl) return 1;
+    if ((double)r > fl) return 0;
+    uint32_t ext[4];
+    philox_at(src->c0, src->cell, src->step, src->tag, src->seed, ext);
+    return (double)ext[src->w] + 0.5 < ldexp(X - fl, 32);
+}
+
+int orc_accept(uint32_t r, double p, uint32_t c0, uint32_t cell, uint64_t step, uint32_t tg, uint64_t seed, int w)
+{
+    accept_src src = { c0, cell, step, tg, seed, w };
+    return accept_u(r, p, &src);
 }
 
 /* Identifier of a secondary: marker bit, step, channel, cell, pair, slot. */
@@ -828,7 +856,7 @@ static void lepton_lab(double T, const double n[3], const frame *f, double out[3
 
 /* One Bremsstrahlung trial on pair j (Eq. proba3 and Sec. III.A). */
 static int brems_pair(pair_ctx *c, int group, orc_species *P, int ip, const orc_species *I, int it,
-                      uint32_t j, double U1, orc_species *ph)
+                      uint32_t j, uint32_t r1, const accept_src *src, orc_species *ph)
 {
     const orc_tables *t = c->t;
     const orc_table_spec *sp = &t->spec;
@@ -838,7 +866,7 @@ static int brems_pair(pair_ctx *c, int group, orc_species *P, int ip, const orc_
     if (sigma <= 0.0) return 0;
     double x = c->coef * sigma * f.pp / (f.gl * f.gi);
     if (x > 1.0) c->st->status |= ORC_ST_PROB_LARGE;
-    if (!(U1 < -expm1(-x))) return 0;
+    if (!accept_u(r1, -expm1(-x), src)) return 0;
     int ch = group == G_EM ? CH_BREMS_EM : CH_BREMS_EP;
     c->st->accepted[ch] += 1;
     uint32_t ev[4];
@@ -866,7 +894,7 @@ static int brems_pair(pair_ctx *c, int group, orc_species *P, int ip, const orc_
 
 /* One Trident trial on pair j (Sec. II.D, "similar scheme" of Sec. III.A). */
 static int trident_pair(pair_ctx *c, int group, orc_species *P, int ip, const orc_species *I, int it,
-                        uint32_t j, double U1, orc_species *em, orc_species *ep)
+                        uint32_t j, uint32_t r1, const accept_src *src, orc_species *em, orc_species *ep)
 {
     const orc_tables *t = c->t;
     const orc_table_spec *sp = &t->spec;
@@ -877,7 +905,7 @@ static int trident_pair(pair_ctx *c, int group, orc_species *P, int ip, const or
     if (sigma <= 0.0) return 0;
     double x = c->coef * sigma * f.pp / (f.gl * f.gi);
     if (x > 1.0) c->st->status |= ORC_ST_PROB_LARGE;
-    if (!(U1 < -expm1(-x))) return 0;
+    if (!accept_u(r1, -expm1(-x), src)) return 0;
     int ch = group == G_EM ? CH_TRI_EM : CH_TRI_EP;
     c->st->accepted[ch] += 1;
     uint32_t e1[4], e2[4];
@@ -905,7 +933,7 @@ static int trident_pair(pair_ctx *c, int group, orc_species *P, int ip, const or
 
 /* One Bethe-Heitler trial on pair j; returns 1 when the photon is absorbed. */
 static int bh_pair(pair_ctx *c, orc_species *ph, int ip, const orc_species *I, int it, uint32_t j,
-                   double U1, orc_species *em, orc_species *ep, int *err)
+                   uint32_t r1, const accept_src *src, orc_species *em, orc_species *ep, int *err)
 {
     const orc_tables *t = c->t;
     const orc_table_spec *sp = &t->spec;
@@ -922,7 +950,7 @@ static int bh_pair(pair_ctx *c, orc_species *ph, int ip, const orc_species *I, i
     if (sigma <= 0.0) return 0;
     double x = c->coef * sigma * kp / (k * f.gi);
     if (x > 1.0) c->st->status |= ORC_ST_PROB_LARGE;
-    if (!(U1 < -expm1(-x))) return 0;
+    if (!accept_u(r1, -expm1(-x), src)) return 0;
     c->st->accepted[CH_BH] += 1;
     uint32_t ev[4];
     philox_at(j, c->cell, c->step, tag(G_BH, PU_EVT_BH, 0), c->seed, ev);
@@ -962,11 +990,14 @@ static void pair_of(uint32_t j, uint32_t Np, uint32_t Nt, const uint32_t rk[4], 
  * species but are not projectiles until the next step; ions are never
  * modified.  Random numbers: Philox4x32-10, key = seed, counter
  *   permutation keys:  (0,      cell, step, group | PERM<<4)
- *   accept U1:         (s>>1,   cell, step, group | ACCEPT<<4 | m<<8),
+ *   accept word r:     (s>>1,   cell, step, group | ACCEPT<<4 | m<<8),
  *                      words 2(s&1) (Brems or BH) and 2(s&1)+1 (Trident),
- *                      s = projectile slot in id order, m = pass index
+ *                      s = projectile slot in id order, m = pass index;
+ *                      its second word r' (only when r = floor(2^32 p)):
+ *                      the same word of (s>>1, cell, step,
+ *                      group | ACCEPT_EXT<<4 | m<<8), see accept_u
  *   event draws:       (j,      cell, step, group | EVT<<4)
- * with U = ((r >> 9) + 1/2) 2^-23.
+ * with U = ((r >> 9) + 1/2) 2^-23 for the event draws.
  */
 int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
              orc_species *em, orc_species *ep, orc_species *ph, const orc_species *ion,
@@ -1019,15 +1050,18 @@ int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
                 uint32_t m = Np >= Nt ? 0 : j / Np;
                 uint32_t acc[4];
                 philox_at(s >> 1, (uint32_t)cell, step, tag(g, PU_ACCEPT, m), seed, acc);
+                accept_src s1 = { s >> 1, (uint32_t)cell, step, tag(g, PU_ACCEPT_EXT, m), seed, (int)(2 * (s & 1)) };
+                accept_src s2 = s1;
+                s2.w += 1;
                 int ip = pidx[s], it = tidx[tau];
                 if (g < 2) {
                     if (mask & ORC_PROC_BREMS)
-                        err |= brems_pair(&c, g, P, ip, ion, it, j, orc_u01(acc[2 * (s & 1)]), ph);
+                        err |= brems_pair(&c, g, P, ip, ion, it, j, acc[2 * (s & 1)], &s1, ph);
                     if (mask & ORC_PROC_TRIDENT)
-                        err |= trident_pair(&c, g, P, ip, ion, it, j, orc_u01(acc[2 * (s & 1) + 1]), em, ep);
+                        err |= trident_pair(&c, g, P, ip, ion, it, j, acc[2 * (s & 1) + 1], &s2, em, ep);
                 } else {
                     if (dead[ip]) continue;
-                    if (bh_pair(&c, P, ip, ion, it, j, orc_u01(acc[2 * (s & 1)]), em, ep, &err)) dead[ip] = 1;
+                    if (bh_pair(&c, P, ip, ion, it, j, acc[2 * (s & 1)], &s1, em, ep, &err)) dead[ip] = 1;
                 }
             }
         }
