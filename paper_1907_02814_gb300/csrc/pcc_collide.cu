@@ -417,11 +417,14 @@ __device__ __noinline__ EventResult bh_event(const StepArgs* ap, Tab<Real> tb, i
 
 // ---- one electron/positron - ion pair: Brems then Trident -------------------
 // The weights (projectile *wp, target ion.w) are read only for accepted
-// pairs; no event writes a live particle's weight.
+// pairs; no event writes a live particle's weight.  rB, rT: the pair's
+// accept words for Brems and Trident; src names the second word of the
+// Brems uniform (the Trident one is the next word of the same draw).
 template <typename Real>
 __device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb, int group, int cell, int mat, Real Zf,
-                                        Real coef, float u[3], const float* wp, float xpos, int t_slot, uint32_t j, Real UB,
-                                        Real UT, Acc& acc, float& rad, float& wcre, bool& had)
+                                        Real coef, float u[3], const float* wp, float xpos, int t_slot, uint32_t j,
+                                        uint32_t rB, uint32_t rT, const AcceptSrc& src, Acc& acc, float& rad,
+                                        float& wcre, bool& had)
 {
     const StepArgs& a = *ap;
     const SpeciesView& ion = a.ion;
@@ -435,7 +438,7 @@ __device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb,
         const Real sig = sigma_at<Real>(tb, tb.bsig + (size_t)mat * a.g.n_rows, a.g, f.Tp, acc.status);
         const Real x = q_div(coef * sig * f.pp, f.gl * f.gi);
         if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
-        if (sig > (Real)0 && UB < x && UB < -expm1(-x)) {
+        if (sig > (Real)0 && accept_u<Real>(rB, -expm1(-x), src, a.step, a.seed)) {
             const int ch = group == kGroupEm ? kChBremsEm : kChBremsEp;
             acc.accepted[ch]++;
             const EventResult r = brems_event<Real>(ap, tb, group, cell, mat, j, *wp, ion.w[t_slot], xpos, f);
@@ -458,7 +461,9 @@ __device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb,
         const Real sig = (Real)5.22e-34 * Zf * Zf * l * l * l;
         const Real x = q_div(coef * sig * f.pp, f.gl * f.gi);
         if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
-        if (sig > (Real)0 && UT < x && UT < -expm1(-x)) {
+        AcceptSrc srcT = src;
+        srcT.w += 1;
+        if (sig > (Real)0 && accept_u<Real>(rT, -expm1(-x), srcT, a.step, a.seed)) {
             const int ch = group == kGroupEm ? kChTriEm : kChTriEp;
             acc.accepted[ch]++;
             const EventResult r = trident_event<Real>(ap, tb, group, cell, j, *wp, ion.w[t_slot], xpos, f);
@@ -544,10 +549,11 @@ __device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
     if (grp.rank() == 0) acc.pairs[group] += Npair;
     if (Npair > 65536u || (uint32_t)cell > 0xFFFFFFu || a.step > 0x7FFFFull) acc.status |= PCC_ST_ID_RANGE;
     const Real Zf = sizeof(Real) == 8 ? (Real)a.screen[(size_t)mat * kScreenFields + 7] : (Real)a.f_Z[mat];
-    // the batched FP32 path rejects from the uniform alone below the bounds
+    // the FP32 path rejects from the accept word alone above the bounds
     const bool quick = sizeof(Real) == 4;
-    const Real bB = quick && (a.mask & PCC_BREMS) ? coef * (Real)a.f_bound[3 * mat] : (Real)0;
-    const Real bT = quick && (a.mask & PCC_TRIDENT) ? coef * (Real)a.f_bound[3 * mat + 1] : (Real)0;
+    const uint32_t kB = quick && (a.mask & PCC_BREMS) ? accept_threshold((float)(coef * (Real)a.f_bound[3 * mat])) : 0u;
+    const uint32_t kT =
+        quick && (a.mask & PCC_TRIDENT) ? accept_threshold((float)(coef * (Real)a.f_bound[3 * mat + 1])) : 0u;
     float rad = 0.f, wcre = 0.f;
     bool had = false;
     const bool has_x = P.x != nullptr;
@@ -565,20 +571,22 @@ __device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
             bool dirty = false;
             if (pr.caseA) {
                 const uint32_t j = pr.pair_of_slot(s);
-                const Real UB = u01<Real>(ac.v[2 * h]), UT = u01<Real>(ac.v[2 * h + 1]);
-                if (!quick || UB < bB || UT < bT) {
+                const uint32_t rB = ac.v[2 * h], rT = ac.v[2 * h + 1];
+                if (!quick || rB <= kB || rT <= kT) {
                     if (quick) acc.candidates[group]++;
-                    ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, &w, xp, t0 + (int)(j % Nt), j, UB, UT, acc,
-                                  rad, wcre, dirty);
+                    const AcceptSrc src{q, (uint32_t)cell, stream_tag(group, kAcceptExt, 0), 2 * h};
+                    ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, &w, xp, t0 + (int)(j % Nt), j, rB, rT, src,
+                                  acc, rad, wcre, dirty);
                 }
             } else {
                 for (uint32_t m = 0, j = s; j < Nt; ++m, j += Np) {
                     const Philox4 am = draw(q, cell, a.step, stream_tag(group, kAccept, m), a.seed);
-                    const Real UB = u01<Real>(am.v[2 * h]), UT = u01<Real>(am.v[2 * h + 1]);
-                    if (quick && !(UB < bB || UT < bT)) continue;
+                    const uint32_t rB = am.v[2 * h], rT = am.v[2 * h + 1];
+                    if (quick && !(rB <= kB || rT <= kT)) continue;
                     acc.candidates[group]++;
+                    const AcceptSrc src{q, (uint32_t)cell, stream_tag(group, kAcceptExt, m), 2 * h};
                     ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, &w, xp, t0 + (int)pr.target_of_pair(j), j,
-                                  UB, UT, acc, rad, wcre, dirty);
+                                  rB, rT, src, acc, rad, wcre, dirty);
                 }
             }
             if (dirty) {
@@ -626,7 +634,7 @@ __device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
     bool absorbed_any = false;
     const bool has_x = P.x != nullptr;
     const bool quick = sizeof(Real) == 4;
-    const Real bBH = quick ? coef * (Real)a.f_bound[3 * mat + 2] : (Real)0;
+    const uint32_t kBH = quick ? accept_threshold((float)(coef * (Real)a.f_bound[3 * mat + 2])) : 0u;
     for (uint32_t q = grp.rank(); 2 * q < Np; q += grp.size()) {
         const int nh = (2 * q + 1 < Np) ? 2 : 1;
         Philox4 ac{};
@@ -639,13 +647,9 @@ __device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
             Real uk[3] = {0, 0, 0}, k = 0;
             for (uint32_t m = 0; m < npass; ++m) {
                 uint32_t j, tau;
-                Real U;
-                if (pr.caseA) {
-                    U = u01<Real>(ac.v[2 * h]);
-                } else {
-                    U = u01<Real>(draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed).v[2 * h]);
-                }
-                if (quick && !(U < bBH)) continue;   // exact quick reject
+                const uint32_t rw =
+                    pr.caseA ? ac.v[2 * h] : draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed).v[2 * h];
+                if (quick && !(rw <= kBH)) continue;   // exact quick reject
                 if (pr.caseA) {
                     j = pr.pair_of_slot(s);
                     tau = j % Nt;
@@ -670,7 +674,8 @@ __device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
                 if (!(sig > (Real)0)) continue;
                 const Real x = coef * sig * kp / (k * f.gi);
                 if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
-                if (!(U < x && U < -expm1(-x))) continue;
+                const AcceptSrc src{q, (uint32_t)cell, stream_tag(kGroupPh, kAcceptExt, m), 2 * h};
+                if (!accept_u<Real>(rw, -expm1(-x), src, a.step, a.seed)) continue;
                 acc.accepted[kChBH]++;
                 const Real fac = d / (f.gi + (Real)1) - k;
                 const Real pv[3] = {uk[0] + fac * f.ui[0], uk[1] + fac * f.ui[1], uk[2] + fac * f.ui[2]};
@@ -1051,8 +1056,8 @@ __device__ __forceinline__ void flag_cell(const Queue& Q, int cell)
     if (atomicCAS(&Q.flag[cell], 0, 1) == 0) Q.flagged[atomicAdd(Q.flagged_count, 1)] = cell;
 }
 
-// Acceptance bounds of the group at this coefficient, as integer thresholds
-// on the 23 uniform bits: U = ((r >> 9) + 1/2) 2^-23 < b  <=>  (r >> 9) < ceil(b 2^23 - 1/2).
+// Acceptance bounds of the group at this coefficient, as thresholds on the
+// accept words: a pair can be accepted only if r <= floor(2^32 b).
 template <int GROUP>
 __device__ __forceinline__ void bound_thresholds(const StepArgs& a, int mat, float coef, uint32_t& k1, uint32_t& k2)
 {
@@ -1064,14 +1069,15 @@ __device__ __forceinline__ void bound_thresholds(const StepArgs& a, int mat, flo
         b1 = (a.mask & PCC_BREMS) ? coef * a.f_bound[3 * mat] : 0.f;
         b2 = (a.mask & PCC_TRIDENT) ? coef * a.f_bound[3 * mat + 1] : 0.f;
     }
-    k1 = (uint32_t)fminf(ceilf(b1 * 8388608.0f - 0.5f), 8388608.0f);
-    k2 = (uint32_t)fminf(ceilf(b2 * 8388608.0f - 0.5f), 8388608.0f);
+    k1 = accept_threshold(b1);
+    k2 = accept_threshold(b2);
 }
 
 // One photon-ion candidate pair (Bethe-Heitler); returns true when the photon
 // is absorbed (its weight is then set to 0 for the compaction).
 __device__ __forceinline__ bool bh_candidate(const StepArgs& a, const Tab<float>& tb, int cell, int mat, float coef,
-                                             int sl, int ts, uint32_t j, float U, Acc& acc, float& wcre)
+                                             int sl, int ts, uint32_t j, uint32_t rw, const AcceptSrc& src, Acc& acc,
+                                             float& wcre)
 {
     const SpeciesView& P = a.ph;
     const SpeciesView& I = a.ion;
@@ -1090,7 +1096,7 @@ __device__ __forceinline__ bool bh_candidate(const StepArgs& a, const Tab<float>
     if (!(sig > 0.f)) return false;
     const float x = q_div(coef * sig * kp, k * f.gi);
     if (x > 1.f) acc.status |= PCC_ST_PROB_LARGE;
-    if (!(U < x && U < -expm1f(-x))) return false;
+    if (!accept_u<float>(rw, -expm1f(-x), src, a.step, a.seed)) return false;
     acc.accepted[kChBH]++;
     const float fac = q_div(d, f.gi + 1.f) - k;
     const float pv[3] = {uk[0] + fac * f.ui[0], uk[1] + fac * f.ui[1], uk[2] + fac * f.ui[2]};
@@ -1288,7 +1294,7 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
             for (int h = 0; h < 2; ++h) {
                 const uint32_t s = base + 2 * gl + h;
                 const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
-                const bool cand = (G == 32 || it < itA) && s < Np && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
+                const bool cand = (G == 32 || it < itA) && s < Np && (r1 <= k1 || r2 <= k2);
                 const unsigned m = __ballot_sync(kFull, cand);
                 if (cand) wb[sw.nb + __popc(m & below)] = make_uint2((uint32_t)cell, s);
                 sw.nb += __popc(m);
@@ -1316,7 +1322,7 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
             for (int h = 0; h < 2; ++h) {
                 const uint32_t s = 2 * q + h, j = s + mp * Np;
                 const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
-                const bool cand = valid && s < Np && j < Nt && ((r1 >> 9) < k1 || (r2 >> 9) < k2);
+                const bool cand = valid && s < Np && j < Nt && (r1 <= k1 || r2 <= k2);
                 const unsigned m = __ballot_sync(kFull, cand);
                 if (cand) Q.qb[t0 + cnt + __popc(m & gmask & below)] = j;
                 cnt += __popc(m & gmask);
@@ -1465,16 +1471,17 @@ __global__ void __launch_bounds__(kBatchedThreads, 4) flat_cand_kernel(const __g
         const int ts = cm.t0 + (int)fast_mod(j, Nt, 1.0f / (float)Nt);
         const Philox4 ph = draw_k(s >> 1, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, 0), a.keys);
         const uint32_t r1 = ph.v[2 * (s & 1u)], r2 = ph.v[2 * (s & 1u) + 1];
+        const AcceptSrc src{s >> 1, (uint32_t)cell, stream_tag(GROUP, kAcceptExt, 0), (int)(2 * (s & 1u))};
         const int sl = cm.p0 + (int)s;
         float rad = 0.f, wcre = 0.f;
         bool event = false;
         if (GROUP == kGroupPh) {
-            event = bh_candidate(a, tb, cell, cm.mat, coef, sl, ts, j, u01<float>(r1), acc, wcre);
+            event = bh_candidate(a, tb, cell, cm.mat, coef, sl, ts, j, r1, src, acc, wcre);
         } else {
             float u[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
             const float xp = P.x ? P.x[sl] : 0.f;
-            ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w + sl, xp, ts, j, u01<float>(r1),
-                           u01<float>(r2), acc, rad, wcre, event);
+            ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w + sl, xp, ts, j, r1, r2, src, acc,
+                           rad, wcre, event);
             if (event) {
                 P.ux[sl] = u[0]; P.uy[sl] = u[1]; P.uz[sl] = u[2];
             }
@@ -1536,17 +1543,18 @@ __global__ void __launch_bounds__(kBatchedThreads, 2) caseb_cand_kernel(const __
                 const uint32_t s = j % Np, mp = j / Np;
                 const Philox4 ph = draw_k(s >> 1, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
                 const uint32_t r1 = ph.v[2 * (s & 1u)], r2 = ph.v[2 * (s & 1u) + 1];
+                const AcceptSrc src{s >> 1, (uint32_t)cell, stream_tag(GROUP, kAcceptExt, mp), (int)(2 * (s & 1u))};
                 const uint32_t t = Nt <= 32 ? (uint32_t)tab[j] : perm_elem_large(j, Nt, rk);
                 const int ts = cm.t0 + (int)t, sl = cm.p0 + (int)s;
                 bool event = false;
                 if (GROUP == kGroupPh) {
                     if (P.w[sl] == 0.f) continue;   // absorbed earlier in this step
-                    event = bh_candidate(a, tb, cell, cm.mat, coef, sl, ts, j, u01<float>(r1), acc, wcre);
+                    event = bh_candidate(a, tb, cell, cm.mat, coef, sl, ts, j, r1, src, acc, wcre);
                 } else {
                     float u[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
                     const float xp = P.x ? P.x[sl] : 0.f;
-                    ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w + sl, xp, ts, j,
-                                   u01<float>(r1), u01<float>(r2), acc, rad, wcre, event);
+                    ei_pair<float>(&a, tb, GROUP, cell, cm.mat, a.f_Z[cm.mat], coef, u, P.w + sl, xp, ts, j, r1, r2,
+                                   src, acc, rad, wcre, event);
                     if (event) {
                         P.ux[sl] = u[0]; P.uy[sl] = u[1]; P.uz[sl] = u[2];
                     }

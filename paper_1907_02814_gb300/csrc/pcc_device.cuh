@@ -21,7 +21,8 @@ constexpr double kPi = 3.14159265358979323846;
 
 // Random-stream tags: group | purpose << 4 | pass << 8 (Philox counter word 3).
 enum Group : uint32_t { kGroupEm = 0, kGroupEp = 1, kGroupPh = 2 };
-enum Purpose : uint32_t { kPerm = 0, kAccept = 1, kEvtBrems = 2, kEvtTri1 = 3, kEvtTri2 = 4, kEvtBH = 5 };
+enum Purpose : uint32_t { kPerm = 0, kAccept = 1, kEvtBrems = 2, kEvtTri1 = 3, kEvtTri2 = 4, kEvtBH = 5,
+                          kAcceptExt = 6 };
 enum Channel : int { kChBremsEm = 0, kChBremsEp = 1, kChTriEm = 2, kChTriEp = 3, kChBH = 4 };
 
 __host__ __device__ __forceinline__ uint32_t stream_tag(uint32_t group, uint32_t purpose, uint32_t pass)
@@ -59,6 +60,46 @@ __device__ __forceinline__ T u01(uint32_t r)
 __device__ __forceinline__ Philox4 draw(uint32_t c0, uint32_t cell, uint64_t step, uint32_t tag, uint64_t seed)
 {
     return philox4x32_10(c0, cell, (uint32_t)step, tag, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Where the second word of an accept uniform comes from: word w of the draw
+// (c0, cell, step, group | kAcceptExt << 4 | pass << 8) of the step's seed.
+struct AcceptSrc {
+    uint32_t c0, cell, tag;
+    int w;
+};
+
+// The accept decision U < p (Eq. proba3: collision with probability
+// p = 1 - exp(-x)) for the uniform U = (2^32 r + r' + 1/2) 2^-64, read digit
+// by digit: the accept word r settles it unless r = floor(2^32 p), and only
+// then (probability 2^-32) is the second word r' drawn.  Every p is honoured
+// down to 2^-64; a fixed-point uniform would drop probabilities below its
+// resolution.  2^32 p and its fractional part are exact in either precision.
+// The tie (r = floor(2^32 p)): the second word against frac(2^32 p) 2^32.
+static __device__ __noinline__ bool accept_tie(double frac32, uint32_t c0, uint32_t cell, uint32_t tag, int w, uint64_t step,
+                                        uint64_t seed)
+{
+    const Philox4 e = draw(c0, cell, step, tag, seed);
+    return (double)e.v[w & 3] + 0.5 < frac32;
+}
+
+template <typename Real>
+__device__ __forceinline__ bool accept_u(uint32_t r, Real p, const AcceptSrc& src, uint64_t step, uint64_t seed)
+{
+    if (!(p > (Real)0)) return false;
+    if (p >= (Real)1) return true;
+    const Real X = p * (Real)4294967296.0, fl = floor(X);
+    const uint32_t u = (uint32_t)fl;
+    if (r != u) return r < u;
+    return accept_tie(ldexp((double)(X - fl), 32), src.c0, src.cell, src.tag, src.w, step, seed);
+}
+
+// Quick-reject threshold on the accept word for a bound b >= p: a pair can
+// only be accepted if r <= floor(2^32 b).
+__device__ __forceinline__ uint32_t accept_threshold(float b)
+{
+    const float X = b * 4294967296.0f;
+    return X >= 4294967040.0f ? 0xFFFFFFFFu : (uint32_t)X;
 }
 
 // The same generator with the ten round keys precomputed (key schedule of
