@@ -188,6 +188,70 @@ def thin_target_photon_beam(ratio, k_mev=100.0, n_cells=16, g_per_cell=64, seed=
     return wl
 
 
+def maxwell_juttner_kinetic(rng, theta, n):
+    """n kinetic energies T (units of m_e c^2) from the isotropic relativistic
+    Maxwell-Juttner law of Eq. (mj), f(gamma) ~ gamma^2 beta exp(-gamma/theta).
+    Rejection: T is proposed from the density ~ (T + 1)^2 exp(-T/theta), a
+    mixture of Gamma(3), Gamma(2) and Gamma(1) laws of scale theta with weights
+    2 theta^3 : 2 theta^2 : theta, and kept with probability
+    beta = sqrt(T (T + 2)) / (T + 1), the ratio of target to proposal."""
+    p = np.array([2.0 * theta ** 3, 2.0 * theta ** 2, theta])
+    p /= p.sum()
+    out = []
+    have = 0
+    while have < n:
+        m = int(1.3 * (n - have)) + 64
+        T = rng.gamma(rng.choice([3.0, 2.0, 1.0], size=m, p=p), theta)
+        keep = rng.uniform(0.0, 1.0, m) < np.sqrt(T * (T + 2.0)) / (T + 1.0)
+        out.append(T[keep])
+        have += int(keep.sum())
+    return np.concatenate(out)[:n]
+
+
+def maxwell_juttner_mean_kinetic(theta):
+    """<T>/m_e c^2 of Eq. (mj): <gamma> - 1 = 3 theta + K1(1/theta)/K2(1/theta) - 1."""
+    from scipy.special import kve
+    return 3.0 * theta + kve(1, 1.0 / theta) / kve(2, 1.0 / theta) - 1.0
+
+
+def maxwell_juttner_theta(mean_kinetic_mev):
+    """The theta whose mean kinetic energy is mean_kinetic_mev."""
+    from scipy.optimize import brentq
+    t = mean_kinetic_mev / MEC2_MEV
+    return brentq(lambda th: maxwell_juttner_mean_kinetic(th) - t, 1e-4, 1e3, xtol=1e-14, rtol=1e-13)
+
+
+def cu_slab_mj(thickness_um, mean_kinetic_mev, e_per_cell=4096, i_per_cell=16, dx_um=0.25, columns=1, seed=6,
+               dt=5e-15):
+    """The fast-electron foil of Sec. IV without fields: a Cu slab
+    (n_i = 8e28 m^-3, Z* = 5, 1 eV) of the given thickness, one cell per dx
+    across it, filled uniformly with isotropic Maxwell-Juttner electrons of
+    the given mean kinetic energy at n_e = 1.5e25 m^-3 x (10 um / thickness),
+    i.e. the constant areal density of the paper's 5, 10 and 15 um runs
+    (3e19, 1.5e19 and 1e19 cm^-3).  ``columns`` independent copies of the
+    slab side by side (cell = column * n_x + i_x) add statistics; positions
+    x in [0, thickness) within each column."""
+    rng = np.random.default_rng(seed)
+    dx = dx_um * 1e-6
+    nx = int(round(thickness_um / dx_um))
+    n_cells = nx * columns
+    n_e, n_i = 1.5e25 * 10.0 / thickness_um, 8e28
+    cell_e = np.repeat(np.arange(n_cells), e_per_cell)
+    T = maxwell_juttner_kinetic(rng, maxwell_juttner_theta(mean_kinetic_mev), len(cell_e))
+    ux, uy, uz = _lepton_from_T(rng, T)
+    x = (cell_e % nx + rng.uniform(0.0, 1.0, len(cell_e))) * dx
+    em = _species(ux, uy, uz, np.full(len(cell_e), n_e / e_per_cell), cell_e, x=x)
+    cell_i = np.repeat(np.arange(n_cells), i_per_cell)
+    iux, iuy, iuz = _maxwellian_ions(rng, len(cell_i), 1.0, MASS_CU)
+    xi = (cell_i % nx + rng.uniform(0.0, 1.0, len(cell_i))) * dx
+    ion = _species(iux, iuy, iuz, np.full(len(cell_i), n_i / i_per_cell), cell_i, x=xi)
+    wl = Workload(f"cu_slab_{thickness_um}um_mj{mean_kinetic_mev}MeV", n_cells, [Material(29, 5.0, n_i, 1.0)],
+                  np.zeros(n_cells, np.int32), MASS_CU, dt, seed, 0, dx=dx)
+    wl.species = {"em": em, "ep": empty_species(True), "ph": empty_species(True), "ion": ion}
+    wl.table["nx"] = nx
+    return wl
+
+
 def au_foil(n_cells=16384, mean_e=256, i_per_cell=64, seed=2, dt=1e-15, dx=2.4e-9):
     """1D Au foil: Poisson(mean_e) electrons per cell, kinetic energy ~ E^-2 on
     0.1-100 MeV, isotropic, weights log-uniform over three decades with mean
