@@ -218,6 +218,19 @@ int pcc_set_schedule(pcc_ctx *ctx, int min_blocks_per_sm, int blocks_per_sm);
  * Asynchronous. */
 int pcc_append_secondaries(pcc_ctx *ctx, int n_cells, pcc_species *sp, void *stream);
 
+/* Diagnostic: the accept decision of the collision kernels (Eq. proba3: a
+ * pair collides if U < p, p = 1 - exp(-x)) for n given accept words r[i] and
+ * probabilities p[i].  U = (2^32 r + r' + 1/2) 2^-64 is compared with p
+ * digit by digit: r settles it unless r = floor(2^32 p); only then is r'
+ * drawn, as word w[i] of the Philox4x32-10 draw with counter
+ * (c0[i], cell[i], step, tag[i]) and key seed.  out64[i]: the decision with
+ * p in FP64 (the plain path); out32[i]: with p rounded to FP32 (the batched
+ * path).  Device arrays of n entries (outputs 0 or 1).  PCC_E_INVALID for
+ * n < 0 or a null array.  Asynchronous. */
+int pcc_accept_check(int n, const uint32_t *r, const double *p, const uint32_t *c0, const uint32_t *cell,
+                     const uint32_t *tag, const int *w, uint64_t step, uint64_t seed, int *out32, int *out64,
+                     void *stream);
+
 /* Diagnostic: the pairing of Sec. III.A for one projectile species against
  * the targets.  For live projectile slot s of cell c (written at index
  * cell_start[c] + s): out_j = its first pair index j, out_t = that pair's
