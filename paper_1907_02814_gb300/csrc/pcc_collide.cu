@@ -1636,31 +1636,44 @@ __device__ void compact_region_warp(const SpeciesView& P, int cell)
     if (lane == 0) P.count[cell] = wr - P.added[cell];
 }
 
-// Cells with an event in this call, one warp each: the Kahan update of the
-// cell ledger from the gathered contributions and (photons) the compaction
-// that removes absorbed photons.
+// Cells with an event in this call: the Kahan update of the cell ledger
+// from the gathered contributions, and (photons) the compaction that removes
+// absorbed photons.  Photon cells take a warp each (the compaction is
+// warp-wide); the other groups' cells take one thread each.
+__device__ __forceinline__ void finalize_ledger(const StepArgs& a, const Queue& Q, int cell)
+{
+    const float2 ev = Q.evacc[cell];
+    if (a.ledger) {
+        float4* Lg = reinterpret_cast<float4*>(a.ledger) + cell;
+        float4 v = *Lg;
+        Kahan ka{v.x, v.y}, kb{v.z, v.w};
+        ka.add(ev.x);
+        kb.add(ev.y);
+        *Lg = make_float4(ka.s, ka.c, kb.s, kb.c);
+    }
+    Q.evacc[cell] = make_float2(0.f, 0.f);
+}
+
 template <int GROUP>
 __global__ void finalize_kernel(const __grid_constant__ StepArgs a, Queue Q)
 {
-    const int lane = threadIdx.x & 31;
     const int n = *Q.flagged_count;
+    if (GROUP != kGroupPh) {
+        for (int kk = blockIdx.x * blockDim.x + threadIdx.x; kk < n; kk += gridDim.x * blockDim.x) {
+            const int cell = Q.flagged[kk];
+            if (cell < 0 || cell >= a.n_cells) continue;
+            finalize_ledger(a, Q, cell);
+            Q.flag[cell] = 0;
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int kk = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); kk < n; kk += nwarps) {
         const int cell = Q.flagged[kk];
         if (cell < 0 || cell >= a.n_cells) continue;
-        if (lane == 0) {
-            const float2 ev = Q.evacc[cell];
-            if (a.ledger) {
-                float4* Lg = reinterpret_cast<float4*>(a.ledger) + cell;
-                float4 v = *Lg;
-                Kahan ka{v.x, v.y}, kb{v.z, v.w};
-                ka.add(ev.x);
-                kb.add(ev.y);
-                *Lg = make_float4(ka.s, ka.c, kb.s, kb.c);
-            }
-            Q.evacc[cell] = make_float2(0.f, 0.f);
-        }
-        if (GROUP == kGroupPh) compact_region_warp(a.ph, cell);
+        if (lane == 0) finalize_ledger(a, Q, cell);
+        compact_region_warp(a.ph, cell);
         __syncwarp();
         if (lane == 0) Q.flag[cell] = 0;
     }
