@@ -848,7 +848,7 @@ template <bool SMEM>
 __global__ void __launch_bounds__(1024) class_offsets_kernel(const __grid_constant__ ClassSort S)
 {
     extern __shared__ int sm[];
-    __shared__ int part[1024];
+    __shared__ int part[32];
     if (!(S.run >> blockIdx.x & 1u)) return;
     const CellList& L = S.L[blockIdx.x];
     const int n = kClasses * L.nblk;
@@ -857,32 +857,51 @@ __global__ void __launch_bounds__(1024) class_offsets_kernel(const __grid_consta
         for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = L.bh[i];
     __syncthreads();
     // scan order: classes from the largest, blocks in order; thread t takes
-    // a contiguous chunk of that order
+    // a contiguous chunk [i0, i1) of that order, entry (class k, block b)
+    // stepped without divisions
     const int per = (n + blockDim.x - 1) / blockDim.x;
-    const int i0 = threadIdx.x * per, i1 = min(i0 + per, n);
+    const int i0 = min((int)threadIdx.x * per, n), i1 = min(i0 + per, n);
+    const int k0 = kClasses - 1 - i0 / L.nblk, b0 = i0 - (kClasses - 1 - k0) * L.nblk;
     int sum = 0;
-    for (int e = i0; e < i1; ++e) sum += v[(kClasses - 1 - e / L.nblk) * L.nblk + e % L.nblk];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive scan of the thread sums
-        const int t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += t;
-        __syncthreads();
+    for (int e = i0, k = k0, b = b0; e < i1; ++e) {
+        sum += v[k * L.nblk + b];
+        if (++b == L.nblk) { b = 0; --k; }
     }
-    int run = part[threadIdx.x] - sum;
-    for (int e = i0; e < i1; ++e) {
-        int& x = v[(kClasses - 1 - e / L.nblk) * L.nblk + e % L.nblk];
+    // exclusive scan of the thread sums: within each warp by shuffles, then
+    // over the warp totals
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) part[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int x = lane < nw ? part[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        part[lane] = x;
+    }
+    __syncthreads();
+    int run = (wid ? part[wid - 1] : 0) + incl - sum;
+    for (int e = i0, k = k0, b = b0; e < i1; ++e) {
+        int& x = v[k * L.nblk + b];
         const int c = x;
         x = run;
         run += c;
+        if (++b == L.nblk) { b = 0; --k; }
     }
     __syncthreads();
     // class k occupies [offset of its block 0, offset of block 0 of class
     // k - 1) of the list; class 0 ends at the total
     if (threadIdx.x < kClasses) {
         const int k = threadIdx.x;
-        const int end = k == 0 ? part[blockDim.x - 1] : v[(k - 1) * L.nblk];
+        const int end = k == 0 ? part[nw - 1] : v[(k - 1) * L.nblk];
         L.hist[k] = end - v[k * L.nblk];
     }
     if (SMEM)
