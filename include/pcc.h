@@ -135,8 +135,8 @@ typedef struct {
     unsigned long long created[5];   /* events kept by the weight correction          */
     double energy_change;            /* sum over events of W (E_out - E_in), m_e c^2 m^-3 */
     double charge_change;            /* sum over events of W (q_out - q_in), e m^-3        */
-    unsigned long long candidates[3];/* batched path: pairs whose uniform fell below the
-                                        per-material bound and were evaluated in full    */
+    unsigned long long candidates[3];/* batched path: pairs whose accept word fell below
+                                        the per-material bound, evaluated in full        */
 } pcc_stats;
 
 /* Library version string and the message of the last synchronous error
@@ -189,15 +189,20 @@ int pcc_bin(pcc_ctx *ctx, const pcc_particles *in, int n_cells, pcc_species *out
  * the secondary energy; secondaries appended to the cell regions (photons
  * from Brems, e-/e+ from Trident and BH); absorbed photons removed.  ion may
  * not be NULL; em, ep, ph may have zero live particles but not be NULL.
+ * A pair collides if U < p, p = 1 - exp(-x), for the uniform
+ * U = (2^32 r + r' + 1/2) 2^-64 compared digit by digit: the pair's accept
+ * word r settles it unless r = floor(2^32 p), and only then is the second
+ * word r' drawn, so even per-pair probabilities far below 1e-7 (small time
+ * steps, rare processes) are honoured (see pcc_accept_check).
  * precision PCC_FP64_PLAIN: one thread block per cell, FP64 arithmetic;
  * PCC_FP32_BATCHED: persistent kernel, FP32 arithmetic, and a pair whose
- * uniform is at or above a per-material bound of its acceptance probability
- * is rejected without being evaluated (exact, since 1 - exp(-x) <= x; the
- * Trident bound assumes ion-frame Lorentz factors below 1e7).  ledger: optional
- * device float[n_cells][4], per cell {radiated photon energy, compensation,
- * created weight, compensation} accumulated with Kahan summation.
- * Random numbers: Philox4x32-10 keyed by `seed`, counters (slot or pair,
- * cell, step, stream tag).  Asynchronous. */
+ * accept word exceeds floor(2^32 b) for a per-material bound b of its
+ * acceptance probability is rejected without being evaluated (exact, since
+ * 1 - exp(-x) <= x <= b; the Trident bound assumes ion-frame Lorentz factors
+ * below 1e7).  ledger: optional device float[n_cells][4], per cell {radiated
+ * photon energy, compensation, created weight, compensation} accumulated
+ * with Kahan summation.  Random numbers: Philox4x32-10 keyed by `seed`,
+ * counters (slot or pair, cell, step, stream tag).  Asynchronous. */
 int pcc_collide(pcc_ctx *ctx, const pcc_cells *cells, pcc_species *em, pcc_species *ep,
                 pcc_species *ph, const pcc_species *ion, double dt, uint64_t seed, uint64_t step,
                 unsigned process_mask, int precision, float *ledger, void *stream);
