@@ -217,6 +217,16 @@ int pcc_collide(pcc_ctx *ctx, const pcc_cells *cells, pcc_species *em, pcc_speci
  * on this context.  PCC_E_INVALID outside these ranges. */
 int pcc_set_schedule(pcc_ctx *ctx, int min_blocks_per_sm, int blocks_per_sm);
 
+/* Fault injection (no counterpart in the paper): the bounded waits of the
+ * batched kernels (the mbarrier of the bulk copy that stages the ln sigma
+ * rows in shared memory) give up after `polls` polls instead of 4194304,
+ * set PCC_ST_TIMEOUT and fall back to the global rows (same values), after
+ * a second bounded wait that lets the copy land.  polls = 0 makes every
+ * staged launch time out, to test the status path without a hang or a
+ * fault.  Applies to later pcc_collide calls on this context; PCC_E_INVALID
+ * for polls < 0. */
+int pcc_set_wait_limit(pcc_ctx *ctx, int polls);
+
 /* Make the secondaries of the last step live (Sec. III.A: created
  * macro-particles join the simulation): per cell, order the appended
  * particles by pid, then cell_count += cell_added, cell_added = 0.

@@ -44,6 +44,7 @@ struct StepArgs {
     DevStats* st;
     PhiloxKeys keys;         // round keys of the seed
     float f_cdt;             // c dt in float
+    int wait_polls;          // bounded waits give up after this many polls
 };
 
 // ---- per-thread accumulators ---------------------------------------------
@@ -929,10 +930,29 @@ __global__ void class_scatter_kernel(const __grid_constant__ ClassSort S)
     }
 }
 
+// Poll the mbarrier at smem address b for phase 0, at most `polls` times;
+// true once the phase has completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t b, int polls)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < polls && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(b)
+            : "memory");
+    }
+    return done != 0;
+}
+
 // Stage the ln sigma rows (n_mat x n_rows floats) in shared memory with one
-// bulk copy; returns the shared copy, or the global one if the wait gives up.
+// bulk copy; returns the shared copy, or the global one if the wait gives up
+// after `polls` polls (status PCC_ST_TIMEOUT).  A block that gave up still
+// waits, bounded again, for its copy to land before going on, so that no
+// copy into its shared memory is left in flight; the global rows hold the
+// same values, so only the status differs.
 __device__ const float* stage_table(const float* src, int bytes, unsigned char* dyn, unsigned long long* bar,
-                                    unsigned& status)
+                                    int polls, unsigned& status)
 {
     if (bytes <= 0) return src;
     const uint32_t b = smem_u32(bar);
@@ -948,17 +968,12 @@ __device__ const float* stage_table(const float* src, int bytes, unsigned char* 
                      "l"(src), "r"(bytes), "r"(b)
                      : "memory");
     }
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(b)
-            : "memory");
-    }
+    const bool done = mbar_wait_bounded(b, polls);
     const int all = __syncthreads_and((int)done);
     if (!all) {
         status |= PCC_ST_TIMEOUT;
+        mbar_wait_bounded(b, 1 << 22);   // let this block's copy land
+        __syncthreads();
         return src;
     }
     return reinterpret_cast<const float*>(dyn);
@@ -1466,7 +1481,7 @@ __global__ void __launch_bounds__(kBatchedThreads, 4) flat_cand_kernel(const __g
     __shared__ __align__(8) unsigned long long bar;
     block_acc_init(bacc);
     unsigned st0 = 0;
-    const float* ls = stage_table(GROUP == kGroupPh ? a.f_bh_lnsig : a.f_brems_lnsig, stage_bytes, dyn, &bar, st0);
+    const float* ls = stage_table(GROUP == kGroupPh ? a.f_bh_lnsig : a.f_brems_lnsig, stage_bytes, dyn, &bar, a.wait_polls, st0);
     if (st0 && threadIdx.x == 0) bacc.status |= st0;
     __syncthreads();
     const Tab<float> tb = batched_tab<GROUP>(a, ls);
@@ -1527,7 +1542,7 @@ __global__ void __launch_bounds__(kBatchedThreads, 2) caseb_cand_kernel(const __
     __shared__ __align__(8) unsigned long long bar;
     block_acc_init(bacc);
     unsigned st0 = 0;
-    const float* ls = stage_table(GROUP == kGroupPh ? a.f_bh_lnsig : a.f_brems_lnsig, stage_bytes, dyn, &bar, st0);
+    const float* ls = stage_table(GROUP == kGroupPh ? a.f_bh_lnsig : a.f_brems_lnsig, stage_bytes, dyn, &bar, a.wait_polls, st0);
     if (st0 && threadIdx.x == 0) bacc.status |= st0;
     __syncthreads();
     const Tab<float> tb = batched_tab<GROUP>(a, ls);
@@ -1760,6 +1775,7 @@ static StepArgs make_args(pcc_ctx* ctx, const pcc_cells* cells, pcc_species* em,
     a.f_bound = ctx->f_bound;
     a.keys = philox_keys(seed);
     a.f_cdt = (float)(kC * dt);
+    a.wait_polls = ctx->wait_polls;
     a.st = ctx->stats;
     return a;
 }
@@ -1965,6 +1981,16 @@ int collide_prepare(pcc_ctx* ctx, const pcc_cells* cells, const pcc_species* em,
     if (run_em) warm_occupancy<kGroupEm>(ctx, stage);
     if (run_ep) warm_occupancy<kGroupEp>(ctx, stage);
     if (run_ph) warm_occupancy<kGroupPh>(ctx, stage);
+    return PCC_OK;
+}
+
+extern "C" int pcc_set_wait_limit(pcc_ctx* ctx, int polls)
+{
+    if (!ctx || polls < 0) {
+        set_error("pcc_set_wait_limit: invalid argument");
+        return PCC_E_INVALID;
+    }
+    ctx->wait_polls = polls;
     return PCC_OK;
 }
 

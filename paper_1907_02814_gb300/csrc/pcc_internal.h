@@ -46,6 +46,7 @@ struct pcc_ctx {
     int minb = 4;                  // register budget: minimum resident blocks per SM
     int blocks_per_sm = 0;         // persistent grid cap (0: as many as fit)
     bool class_smem_ready = false; // large shared memory enabled for the class-sort offsets
+    int wait_polls = 1 << 22;      // bounded waits give up after this many polls (fault injection: 0)
     // resident blocks per SM of the persistent kernels, by (kernel, dynamic smem)
     struct Occ { const void* fn; int smem; int per_sm; };
     std::vector<Occ> occ;

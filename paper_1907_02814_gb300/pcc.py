@@ -76,6 +76,7 @@ EXPORTS = {
                               C.POINTER(Species), C.c_double, C.c_uint64, C.c_uint64, C.c_uint, C.c_int, _vp, _vp]),
     "pcc_append_secondaries": (C.c_int, [_vp, C.c_int, C.POINTER(Species), _vp]),
     "pcc_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "pcc_set_wait_limit": (C.c_int, [_vp, C.c_int]),
     "pcc_pairing": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.POINTER(Species), C.c_int, C.c_uint64,
                               C.c_uint64, _vp, _vp, _vp]),
     "pcc_totals": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.c_int, _vp, _vp]),
@@ -186,6 +187,10 @@ class Context:
 
     def set_schedule(self, min_blocks_per_sm=4, blocks_per_sm=0):
         _check(self.lib.pcc_set_schedule(self.h, int(min_blocks_per_sm), int(blocks_per_sm)), "pcc_set_schedule")
+
+    def set_wait_limit(self, polls=1 << 22):
+        """Fault injection: bounded waits give up after `polls` polls (0: at once)."""
+        _check(self.lib.pcc_set_wait_limit(self.h, int(polls)), "pcc_set_wait_limit")
 
     def steps_capture(self, n_cells, material_of_cell, ion_mass, em, ep, ph, ion, dt, seed, step0, n_steps,
                       mask=BREMS | TRIDENT | BH, precision=FP32_BATCHED, ledger=None, timing=False, stream=None):
