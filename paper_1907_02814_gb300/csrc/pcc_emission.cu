@@ -445,7 +445,7 @@ __device__ __forceinline__ void nr_sample(const EmArgs& a, double g, double bw, 
 constexpr int kSums = 11;
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kEmThreads, GRAD ? 2 : 3) emission_kernel(const __grid_constant__ EmArgs a)
+__global__ void __launch_bounds__(kEmThreads, GRAD ? 2 : 4) emission_kernel(const __grid_constant__ EmArgs a)
 {
     __shared__ double part[kEmWarps][kSums];
     const int c = blockIdx.x;
