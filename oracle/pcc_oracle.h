@@ -14,9 +14,11 @@
  *
  * Parity pins: every formula function is pinned by the CPU tests against
  * quadrature of its integral definition, a textbook limit, a closed-form
- * invariant or a value printed in the paper.  The Trident pair-energy and
- * split shapes (Sec. II.D) have no such pin: "parity unpinned" (only
- * normalisation and monotonicity of their CDFs are checked).
+ * invariant or a value printed in the paper.  The Trident shapes (Sec. II.D)
+ * are pinned by limits: the pair-energy spectrum integrates to the
+ * Landau-Lifshitz leading-logarithm total at large gamma_1 and rises as the
+ * low-energy Bhabha form E_p^3 at threshold; the split CDF equals its exact
+ * antiderivative.
  */
 #ifndef PCC_ORACLE_H
 #define PCC_ORACLE_H

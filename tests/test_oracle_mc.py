@@ -64,8 +64,9 @@ def test_bh_table_matches_quadrature(orc, cu_tables):
 
 
 def test_trident_tables_normalised_and_monotone(cu_tables):
-    """Trident pair-energy and split CDFs: parity unpinned beyond being
-    normalised, monotone and (split) symmetric about gamma_p/2."""
+    """Trident pair-energy and split CDFs: normalised, monotone and (split)
+    symmetric about gamma_p/2.  Their values are pinned in
+    test_oracle_trident.py (exact antiderivative, adaptive quadrature)."""
     T = cu_tables
     for F in (T.tri_gp_cdf, T.tri_split_cdf):
         assert np.all(F[:, 0] == 0.0) and np.all(F[:, -1] == 1.0)

@@ -352,7 +352,8 @@ def test_bh_total_vanishes_at_threshold(orc):
 
 def test_trident_total(orc):
     """Sec. II.D fit: zero below the pair threshold gamma = 3, positive and
-    increasing above (values unpinned beyond the fit itself)."""
+    increasing above; its size against the leading-log total is pinned in
+    test_oracle_trident.py."""
     assert orc.sigma_trident(29, 2.9) == 0.0
     v = [orc.sigma_trident(29, g) for g in (3.0, 10.0, 100.0, 1000.0)]
     assert all(a < b for a, b in zip(v, v[1:])) and v[0] > 0
@@ -362,7 +363,8 @@ def test_trident_total(orc):
 def test_trident_shapes(orc):
     """Pair-energy spectrum vanishes at threshold and at the kinematic edge;
     the split shape is symmetric in gamma_+ <-> gamma_p - gamma_+ and not
-    negative (parity unpinned beyond these properties)."""
+    negative; the spectrum's limits and the split CDF are pinned in
+    test_oracle_trident.py."""
     for g1 in (5.0, 50.0, 500.0):
         assert orc.dsdgp_trident(29, g1, 2.0) == 0.0 and orc.dsdgp_trident(29, g1, g1 - 1.0) == 0.0
         assert orc.dsdgp_trident(29, g1, 0.5 * (g1 + 1)) > 0
