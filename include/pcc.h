@@ -144,6 +144,16 @@ typedef struct {
 const char *pcc_version(void);
 const char *pcc_last_error(void);
 
+/* Name and one-line meaning of a return code ("PCC_E_CAPACITY: ...");
+ * "unknown return code" for any value outside pcc_status.  Static storage,
+ * never NULL, needs no device. */
+const char *pcc_status_string(int code);
+
+/* Name of one bit of the device status word ("PCC_ST_TIMEOUT");
+ * "unknown status bit" unless exactly one PCC_ST_* bit is set.  Static
+ * storage, never NULL, needs no device. */
+const char *pcc_status_bit_string(unsigned bit);
+
 /* Create a context on CUDA device `device`; it owns the tables, the device
  * status word, step counters and scratch buffers.  Returns PCC_E_CUDA when
  * the device is unusable.  Destroy with pcc_destroy (NULL is accepted). */

@@ -46,6 +46,31 @@ extern "C" const char* pcc_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" unsigned long long pcc_launch_count(void) { return launches_so_far(); }
 
+extern "C" const char* pcc_status_string(int code)
+{
+    switch (code) {
+    case PCC_OK: return "PCC_OK: success";
+    case PCC_E_INVALID: return "PCC_E_INVALID: bad argument";
+    case PCC_E_CUDA: return "PCC_E_CUDA: a CUDA runtime call failed";
+    case PCC_E_CAPACITY: return "PCC_E_CAPACITY: a buffer or supported size is too small";
+    case PCC_E_NO_TABLES: return "PCC_E_NO_TABLES: tables not built on this context";
+    default: return "unknown return code";
+    }
+}
+
+extern "C" const char* pcc_status_bit_string(unsigned bit)
+{
+    switch (bit) {
+    case PCC_ST_TABLE_RANGE: return "PCC_ST_TABLE_RANGE";
+    case PCC_ST_PROB_LARGE: return "PCC_ST_PROB_LARGE";
+    case PCC_ST_CAPACITY: return "PCC_ST_CAPACITY";
+    case PCC_ST_NONFINITE: return "PCC_ST_NONFINITE";
+    case PCC_ST_ID_RANGE: return "PCC_ST_ID_RANGE";
+    case PCC_ST_TIMEOUT: return "PCC_ST_TIMEOUT";
+    default: return "unknown status bit";
+    }
+}
+
 extern "C" int pcc_create(pcc_ctx** out, int device)
 {
     if (!out) { set_error("pcc_create: null output"); return PCC_E_INVALID; }

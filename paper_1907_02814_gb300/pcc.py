@@ -67,6 +67,8 @@ _lib = None
 EXPORTS = {
     "pcc_version": (C.c_char_p, []),
     "pcc_last_error": (C.c_char_p, []),
+    "pcc_status_string": (C.c_char_p, [C.c_int]),
+    "pcc_status_bit_string": (C.c_char_p, [C.c_uint]),
     "pcc_create": (C.c_int, [C.POINTER(_vp), C.c_int]),
     "pcc_destroy": (None, [_vp]),
     "pcc_tables_build": (C.c_int, [_vp, C.POINTER(Material), C.c_int, C.POINTER(TableSpec), _vp]),
@@ -114,10 +116,21 @@ class PccError(RuntimeError):
     pass
 
 
+def status_string(code: int) -> str:
+    """Name and meaning of a return code of the C ABI."""
+    return load().pcc_status_string(int(code)).decode()
+
+
+def status_bits(status: int) -> list[str]:
+    """Names of the bits set in a device status word (pcc_read_status)."""
+    L = load()
+    return [L.pcc_status_bit_string(1 << b).decode() for b in range(32) if (int(status) >> b) & 1]
+
+
 def _check(rc, what):
     if rc != PCC_OK:
         msg = load().pcc_last_error().decode()
-        raise PccError(f"{what} failed with status {rc}: {msg}")
+        raise PccError(f"{what} failed with {status_string(rc)}: {msg}")
 
 
 def _ptr(t):

@@ -39,6 +39,15 @@ int main(void)
         ++failures;
     }
 
+    /* return-code and status-bit names */
+    if (strncmp(pcc_status_string(PCC_E_CAPACITY), "PCC_E_CAPACITY", 14) != 0 ||
+        strcmp(pcc_status_string(99), "unknown return code") != 0 ||
+        strcmp(pcc_status_bit_string(PCC_ST_TIMEOUT), "PCC_ST_TIMEOUT") != 0 ||
+        strcmp(pcc_status_bit_string(PCC_ST_TIMEOUT | PCC_ST_CAPACITY), "unknown status bit") != 0) {
+        fprintf(stderr, "status strings\n");
+        ++failures;
+    }
+
     pcc_ctx *ctx = (pcc_ctx *)&failures;   /* must be overwritten with NULL */
     expect(pcc_create(NULL, 0), PCC_E_INVALID, "pcc_create");
     int rc = pcc_create(&ctx, -1);

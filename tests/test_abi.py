@@ -53,3 +53,25 @@ def test_null_arguments_rejected_without_a_device(lib):
     assert L.pcc_tables_build(None, None, 0, None, None) == pcc.PCC_E_INVALID
     assert L.pcc_collide(None, None, None, None, None, None, 1.0, 0, 0, 7, 0, None, None) == pcc.PCC_E_INVALID
     assert b"invalid" in L.pcc_last_error()
+
+
+def test_status_strings_without_a_device(lib):
+    from paper_1907_02814_gb300 import pcc
+    L = pcc.load()
+    names = {pcc.PCC_OK: "PCC_OK", pcc.PCC_E_INVALID: "PCC_E_INVALID", 2: "PCC_E_CUDA", 3: "PCC_E_CAPACITY",
+             4: "PCC_E_NO_TABLES"}
+    for code, name in names.items():
+        assert L.pcc_status_string(code).decode().startswith(name + ": ")
+    assert L.pcc_status_string(5) == b"unknown return code"
+    assert L.pcc_status_string(-1) == b"unknown return code"
+    bits = {pcc.ST_TABLE_RANGE: "PCC_ST_TABLE_RANGE", pcc.ST_PROB_LARGE: "PCC_ST_PROB_LARGE",
+            pcc.ST_CAPACITY: "PCC_ST_CAPACITY", pcc.ST_NONFINITE: "PCC_ST_NONFINITE",
+            pcc.ST_ID_RANGE: "PCC_ST_ID_RANGE", pcc.ST_TIMEOUT: "PCC_ST_TIMEOUT"}
+    for bit, name in bits.items():
+        assert L.pcc_status_bit_string(bit).decode() == name
+    assert L.pcc_status_bit_string(0) == b"unknown status bit"
+    assert L.pcc_status_bit_string(3) == b"unknown status bit"
+    assert L.pcc_status_bit_string(0x40) == b"unknown status bit"
+    assert pcc.status_bits(pcc.ST_TIMEOUT | pcc.ST_TABLE_RANGE) == ["PCC_ST_TABLE_RANGE", "PCC_ST_TIMEOUT"]
+    with pytest.raises(pcc.PccError, match="PCC_E_INVALID"):
+        pcc._check(L.pcc_create(None, 0), "pcc_create")
