@@ -18,7 +18,7 @@
 
 #include "pcc_oracle.h"
 
-/* SplitMix64: the driver's own input generator (Steele et al., 2014). */
+/* SplitMix64: this program's own input generator (Steele et al., 2014). */
 static uint64_t sm_state = 0x9E3779B97F4A7C15ull;
 static uint64_t sm_next(void)
 {

@@ -7,7 +7,7 @@ empty, single-particle and ion-free cells, ragged counts, energies above
 the table, a step long enough that every pair collides, a photon store
 that overflows, both screening modes and both nonrelativistic bounds.  It
 also checks, with -Wall -Wextra -Werror, that the oracle compiles without
-warnings.  Running the driver natively keeps the sanitizer runtimes out of
+warnings.  Running the C programs natively keeps the sanitizer runtimes out of
 the Python process."""
 import os
 import shutil
