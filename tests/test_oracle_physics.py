@@ -343,6 +343,54 @@ def test_bh_symmetry_threshold_and_unscreened_limit(orc):
             assert orc.dsdg_bh(u, k, gp) == pytest.approx(ref, rel=1e-3)
 
 
+def _complete_screening_log(s):
+    """I_R + 1, which takes the place of the textbook radiation logarithm
+    ln(183 Z^-1/3) in the paper's notation (L_TF without the 0.885 factor)."""
+    L = s.LR
+    return 0.5 * (math.log1p(L * L) - L * L / (1 + L * L)) + 1.0
+
+
+@pytest.mark.parametrize("Z,Zs,T", [(29, 0.0, 0.0), (29, 5.0, 100.0), (79, 20.0, 1000.0), (13, 3.0, 10.0)])
+def test_bh_total_complete_screening(orc, Z, Zs, T):
+    """k -> infinity: the BH total tends to Bethe and Heitler's
+    complete-screening result (28/9) Z^2 alpha r_e^2 [log - 1/42], with the
+    paper's logarithm I_R + 1; the excess falls as 1/k.  The -1/42 comes
+    from the relative weight 2/3 and the constants 1 and 5/6 of the two
+    brackets, none of which this limit takes from the oracle."""
+    from scipy.integrate import quad
+    s = orc.screening(orc.material(Z, Zs, 8.5e28, T))
+    ref = 28.0 / 9.0 * Z * Z * ALPHA * R_E ** 2 * (_complete_screening_log(s) - 1.0 / 42.0)
+    devs = []
+    for k in (1e6, 1e8):
+        f = lambda t: orc.dsdg_bh(s, k, 1.0 + t * (k - 2.0)) * (k - 2.0)
+        cuts = (0.0, 1e-6, 1e-3, 0.5, 1 - 1e-3, 1 - 1e-6, 1.0)
+        tot = sum(quad(f, a, b, epsrel=1e-12, limit=400)[0] for a, b in zip(cuts, cuts[1:]))
+        devs.append(tot / ref - 1.0)
+    assert abs(devs[0]) < 5e-4 and abs(devs[1]) < 1e-5
+    assert abs(devs[1]) < abs(devs[0]) / 30.0
+
+
+@pytest.mark.parametrize("Z,Zs,T", [(29, 0.0, 0.0), (29, 5.0, 100.0), (79, 20.0, 1000.0), (13, 3.0, 10.0)])
+def test_radiative_loss_complete_screening(orc, Z, Zs, T):
+    """gamma_1 -> infinity: the radiated energy per unit path over the
+    electron energy, (1/gamma_1) int k dsigma_B/dk dk, tends to the
+    complete-screening value 4 Z^2 alpha r_e^2 [log - f_C + 1/18] (the
+    inverse radiation length per atom), with the paper's logarithm I_R + 1
+    and its Coulomb correction."""
+    from scipy.integrate import quad
+    s = orc.screening(orc.material(Z, Zs, 8.5e28, T))
+    devs = []
+    for g1 in (1e5, 1e7):
+        ref = 4.0 * Z * Z * ALPHA * R_E ** 2 * (_complete_screening_log(s) - s.fC + 1.0 / 18.0) * g1
+        T1 = g1 - 1.0
+        f = lambda t: orc.dsdk_brems(s, g1, math.exp(t) * T1) * (math.exp(t) * T1) ** 2
+        cuts = (math.log(1e-7), -10.0, -3.0, -1e-3, -1e-7, 0.0)
+        tot = sum(quad(f, a, b, epsrel=1e-12, limit=400)[0] for a, b in zip(cuts, cuts[1:]))
+        devs.append(tot / ref - 1.0)
+    assert abs(devs[0]) < 2e-3 and abs(devs[1]) < 5e-5
+    assert abs(devs[1]) < abs(devs[0]) / 30.0
+
+
 def test_bh_total_vanishes_at_threshold(orc):
     s = orc.screening(orc.material(29, 5, 8.5e28, 100.0))
     tot = [quad(lambda g: orc.dsdg_bh(s, k, g), 1.0, k - 1.0, epsrel=1e-10) for k in (2.0001, 2.01, 2.1)]
