@@ -2,7 +2,8 @@
 cell, slot or pair), so ranks that each own a range of cells (keeping the
 global cell indices) reproduce the single-process step bit for bit.  Run as
 world_size-2 gloo process groups on the CPU with the oracle; the same keying
-is what makes the CUDA path's replicas independent."""
+is what makes the CUDA path's replicas independent.  The conservation
+ledger is the one collective: a 3-double FP64 all-reduce over the ranks."""
 import json
 import os
 import subprocess
@@ -38,6 +39,23 @@ def _run(wl, cells, steps=2):
     return {k: sp[k].canonical() for k in ("em", "ep", "ph")}
 
 
+def _totals(species):
+    """FP64 conservation ledger of a population: total energy (rest mass
+    included, in m_e c^2 per m^3), charge (in e per m^3) and weight."""
+    e = 0.0
+    q = 0.0
+    n = 0.0
+    for k, charge in (("em", -1.0), ("ep", 1.0), ("ph", 0.0)):
+        d = species[k]
+        u2 = d["ux"].astype(np.float64) ** 2 + d["uy"].astype(np.float64) ** 2 + d["uz"].astype(np.float64) ** 2
+        w = d["w"].astype(np.float64)
+        energy = np.sqrt(u2) if k == "ph" else np.sqrt(1.0 + u2)
+        e += float(np.sum(w * energy))
+        q += charge * float(np.sum(w))
+        n += float(np.sum(w))
+    return [e, q, n]
+
+
 def _rank_main(rank, world, port, q):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
@@ -48,8 +66,11 @@ def _rank_main(rank, world, port, q):
     mine = _run(wl, cells)
     got = [None] * world
     dist.all_gather_object(got, mine)
+    # the ledger's one collective: a 3-double FP64 sum over the ranks
+    ledger = torch.tensor(_totals(mine), dtype=torch.float64)
+    dist.all_reduce(ledger)
     if rank == 0:
-        q.put(got)
+        q.put((got, ledger.tolist()))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -65,7 +86,7 @@ def test_two_gloo_ranks_reproduce_single_process_step():
     procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    got = q.get(timeout=300)
+    got, ledger = q.get(timeout=300)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
@@ -78,6 +99,8 @@ def test_two_gloo_ranks_reproduce_single_process_step():
         for f in ("pid", "cell", "ux", "uy", "uz", "w"):
             assert np.array_equal(merged[f][order], whole[k][f]), (k, f)
     assert np.count_nonzero(whole["ph"]["pid"] >> np.uint64(63)) > 0
+    # the all-reduced ledger equals the single-process one up to summation order
+    assert ledger == pytest.approx(_totals(whole), rel=1e-13, abs=1e-13 * abs(_totals(whole)[0]))
 
 
 def test_reference_arm_under_two_ranks_prints_one_line():
