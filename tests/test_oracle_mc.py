@@ -90,6 +90,40 @@ def test_sampler_reproduces_row_cdf(orc, cu_tables):
     assert xs.min() >= T.spec.x_min and xs.max() <= 1.0
 
 
+@pytest.mark.parametrize("table", ["TB_BREMS", "TB_BH", "TB_TRI_GP", "TB_TRI_SPLIT"])
+def test_sampler_mixes_neighbour_rows(orc, cu_tables, table):
+    """Between rows j and j+1, at fractional log position f, the stochastic
+    row pick of reading R10 makes the samples follow (1-f) F_j + f F_{j+1},
+    each row's CDF interpolated linearly in the column's spacing variable
+    (ln y for the log-spaced Brems and Trident pair-energy columns, y for BH
+    and the split).  Checked by KS on every table kind."""
+    T = cu_tables
+    tb = getattr(orc, table)
+    arr = {"TB_BREMS": T.brems_cdf[1], "TB_BH": T.bh_cdf[1], "TB_TRI_GP": T.tri_gp_cdf,
+           "TB_TRI_SPLIT": T.tri_split_cdf}[table]
+    mat = 1 if table in ("TB_BREMS", "TB_BH") else 0
+    j, f = 47, 0.3
+    r = T.row_value(j) * (T.row_value(j + 1) / T.row_value(j)) ** f
+    rng = np.random.default_rng(12)
+    u = rng.uniform(size=(5000, 2))
+    xs = np.array([T.sample(tb, mat, r, a, b) for a, b in u])
+    grid = np.array([T.col_value(tb, c) for c in range(T.spec.n_cols)])
+    is_log = table in ("TB_BREMS", "TB_TRI_GP")
+    tr = np.log if is_log else (lambda v: v)
+    cdf = lambda x: (1 - f) * np.interp(tr(x), tr(grid), arr[j]) + f * np.interp(tr(x), tr(grid), arr[j + 1])
+    assert stats.kstest(xs, cdf).pvalue > 1e-3
+    assert xs.min() >= grid[0] and xs.max() <= grid[-1]
+    # the pick itself: u_row just below f takes row j+1, just above takes row j,
+    # and each inverts its row's CDF by linear interpolation
+    for uc in np.linspace(0.03, 0.97, 11):
+        for row, ur in ((j + 1, f - 1e-9), (j, f + 1e-9)):
+            F = arr[row]
+            lo = np.searchsorted(F, uc, side="right") - 1
+            v = tr(grid[lo]) + (uc - F[lo]) / (F[lo + 1] - F[lo]) * (tr(grid[lo + 1]) - tr(grid[lo]))
+            want = np.exp(v) if is_log else v
+            assert T.sample(tb, mat, r, ur, uc) == pytest.approx(want, rel=1e-12, abs=1e-15), (row, uc)
+
+
 def test_sigma_lookup_interpolation(orc, cu_tables):
     """Log-log interpolation is exact at rows, zero below the table and
     flags the range above it."""
