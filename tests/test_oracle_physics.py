@@ -444,6 +444,29 @@ def test_lorentz_transform(orc):
     assert np.array_equal(orc.boost(np.zeros(3), v), v)
 
 
+
+def test_photon_doppler_shift(orc):
+    """Photons into the ion frame (reading R9): the relativistic Doppler
+    shift k' = k gamma_i (1 - beta_i . n), a null vector stays null, and
+    the aberrated direction obeys the textbook cos theta' =
+    (cos theta - beta) / (1 - beta cos theta) about the ion velocity."""
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        ui = rng.normal(0, 0.5, 3)
+        gi = math.sqrt(1 + ui @ ui)
+        bi = ui / gi
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        k = rng.uniform(0.1, 100.0)
+        out = orc.boost(ui, np.concatenate([[k], k * n]))
+        assert out[0] == pytest.approx(k * gi * (1 - bi @ n), rel=1e-12)
+        assert abs(out[0] ** 2 - out[1:] @ out[1:]) <= 1e-10 * out[0] ** 2
+        b = np.linalg.norm(bi)
+        c = (n @ bi) / b
+        cp = (out[1:] @ bi) / (b * np.linalg.norm(out[1:]))
+        assert cp == pytest.approx((c - b) / (1 - b * c), abs=1e-10)
+
+
 # --------------------------------------------------------- quadrature ----
 def test_gauss_legendre(orc):
     for n in (1, 2, 8, 16, 64):
