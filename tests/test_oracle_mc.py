@@ -177,6 +177,39 @@ def _run(orc, wl, steps, mask, spec=None, cap_extra=20000):
     return T, sp, ledger, tot
 
 
+@pytest.mark.parametrize("u_ion", [1.0, -1.0])
+def test_bh_rate_on_moving_ions_has_the_moller_flux(orc, u_ion):
+    """Photons of k = 20 along +z on ions all moving along z with u = +-1
+    (readings R8, R9): the collision rate is n_g n_i sigma(k') c (1 - beta_i . n),
+    sigma at the Doppler-shifted ion-frame energy k' = k gamma_i (1 - beta_i . n)
+    and the flux factor of a massless projectile on a moving target.
+    Accepted events against that expectation, 4 sigma."""
+    from paper_1907_02814_gb300 import workloads as W
+    n_cells, N, k, w = 200, 256, 20.0, 2e26
+    cell = np.repeat(np.arange(n_cells), N)
+    z = np.zeros(len(cell))
+    ph = W._species(z, z, np.full(len(cell), k), np.full(len(cell), w), cell)
+    ion = W._species(z, z, np.full(len(cell), u_ion), np.full(len(cell), w), cell, pid0=10 ** 7)
+    g_i = math.sqrt(1.0 + u_ion * u_ion)
+    flux = 1.0 - u_ion / g_i                        # 1 - beta_i . n, n = +z
+    kp = k * g_i * flux
+    T = orc.OracleTables([orc.material(29, 0, 8.5e28, 0.0)], orc.table_spec(n_rows=128, n_cols=64))
+    sigma, st_ = T.sigma_lookup(orc.TB_BH, 0, kp - 2.0)
+    assert st_ == 0 and sigma > 0
+    dt = 0.02 / (N * w * sigma * C_LIGHT * flux)      # x = 0.02 per pair
+    x = N * w * sigma * C_LIGHT * flux * dt
+    sp = {"em": orc.OracleSpecies(W.empty_species(), cap=100000), "ep": orc.OracleSpecies(W.empty_species(), cap=100000),
+          "ph": orc.OracleSpecies(ph), "ion": orc.OracleSpecies(ion)}
+    _, st = orc.step(T, n_cells, np.zeros(n_cells, np.int32), sp["em"], sp["ep"], sp["ph"], sp["ion"], 1e5, dt, 3, 0,
+                     mask=orc.PROC_BH)
+    pairs = n_cells * N
+    assert st["pairs"][2] == pairs
+    expect = pairs * -math.expm1(-x)
+    got = st["accepted"][4]
+    assert abs(got - expect) < 4.0 * math.sqrt(expect), (got, expect)
+    assert st["created"][4] == got                   # equal weights: every accepted event is created
+
+
 @pytest.mark.slow
 def test_thin_target_yield_independent_of_weight_ratio(orc):
     """Fig. valid_brem_tf: a 40 MeV beam in neutral Cu (n_e = 1e21 cm^-3,
