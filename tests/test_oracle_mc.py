@@ -210,6 +210,46 @@ def test_bh_rate_on_moving_ions_has_the_moller_flux(orc, u_ion):
     assert st["created"][4] == got                   # equal weights: every accepted event is created
 
 
+@pytest.mark.parametrize("ui", [(0.0, 0.0, 0.6), (0.0, 0.0, -0.6), (0.8, 0.0, 0.0)])
+def test_brems_rate_on_moving_ions_has_the_moller_flux(orc, ui):
+    """Electrons of gamma = 20 along +z on ions all moving with momentum ui
+    (Eq. proba3 and reading R7): the collision rate is n_e n_i sigma(gamma')
+    v_M with Moller's invariant flux v_M = sqrt(|v_e - v_i|^2 - |v_e x v_i|^2/c^2)
+    written in lab velocities, and sigma at the ion-frame Lorentz factor
+    gamma' = gamma_e gamma_i (1 - beta_e . beta_i).  4 sigma."""
+    from paper_1907_02814_gb300 import workloads as W
+    n_cells, N, w, ge = 200, 256, 2e26, 20.0
+    cell = np.repeat(np.arange(n_cells), N)
+    z = np.zeros(len(cell))
+    ue = math.sqrt(ge * ge - 1.0)
+    em = W._species(z, z, np.full(len(cell), ue), np.full(len(cell), w), cell)
+    ion = W._species(np.full(len(cell), ui[0]), np.full(len(cell), ui[1]), np.full(len(cell), ui[2]),
+                     np.full(len(cell), w), cell, pid0=10 ** 7)
+    # float32 storage of the inputs, as the step reads them
+    u_e = np.array([0.0, 0.0, float(np.float32(ue))])
+    u_i = np.array([float(np.float32(v)) for v in ui])
+    g_e, g_i = math.sqrt(1 + u_e @ u_e), math.sqrt(1 + u_i @ u_i)
+    b_e, b_i = u_e / g_e, u_i / g_i
+    v_m = math.sqrt((b_e - b_i) @ (b_e - b_i) - np.cross(b_e, b_i) @ np.cross(b_e, b_i))   # units of c
+    g_p = g_e * g_i * (1.0 - b_e @ b_i)
+    T = orc.OracleTables([orc.material(29, 0, 8.5e28, 0.0)], orc.table_spec(n_rows=128, n_cols=64))
+    sigma, st_ = T.sigma_lookup(orc.TB_BREMS, 0, g_p - 1.0)
+    assert st_ == 0 and sigma > 0
+    dt = 0.02 / (N * w * sigma * C_LIGHT * v_m)
+    x = N * w * sigma * C_LIGHT * v_m * dt
+    sp = {"em": orc.OracleSpecies(em), "ep": orc.OracleSpecies(W.empty_species()),
+          "ph": orc.OracleSpecies(W.empty_species(), cap=100000), "ion": orc.OracleSpecies(ion)}
+    _, st = orc.step(T, n_cells, np.zeros(n_cells, np.int32), sp["em"], sp["ep"], sp["ph"], sp["ion"], 1e5, dt, 4, 0,
+                     mask=orc.PROC_BREMS)
+    pairs = n_cells * N
+    assert st["pairs"][0] == pairs
+    # pairs within one cell share a projectile only once each (N_e = N_i), so
+    # every pair sees the unrecoiled electron
+    expect = pairs * -math.expm1(-x)
+    got = st["accepted"][0]
+    assert abs(got - expect) < 4.0 * math.sqrt(expect), (got, expect)
+
+
 @pytest.mark.slow
 def test_thin_target_yield_independent_of_weight_ratio(orc):
     """Fig. valid_brem_tf: a 40 MeV beam in neutral Cu (n_e = 1e21 cm^-3,
