@@ -250,6 +250,82 @@ def test_brems_rate_on_moving_ions_has_the_moller_flux(orc, ui):
     assert abs(got - expect) < 4.0 * math.sqrt(expect), (got, expect)
 
 
+def _one_pair_per_cell(W, n_cells, proj_u, w=1e27, seed=21):
+    cell = np.arange(n_cells)
+    z = np.zeros(n_cells)
+    proj = W._species(proj_u[:, 0], proj_u[:, 1], proj_u[:, 2], np.full(n_cells, w), cell)
+    ion = W._species(z, z, z, np.full(n_cells, w), cell, pid0=10 ** 7)
+    return proj, ion
+
+
+def _unit(u):
+    u = np.asarray(u, np.float64)
+    return u / np.linalg.norm(u, axis=1, keepdims=True)
+
+
+def test_secondary_kinematics_with_ions_at_rest(orc):
+    """Sec. III.A, ions at rest, one electron and one photon per cell and a
+    step long enough that every pair collides: a Brems photon leaves along
+    the electron, which keeps its direction and loses the photon's energy; a
+    Trident pair leaves along the electron, which pays the pair's energy;
+    a BH pair leaves along the photon and shares its energy."""
+    from paper_1907_02814_gb300 import workloads as W
+    rng = np.random.default_rng(31)
+    n = 300
+    nx, ny, nz = W._isotropic(rng, n)
+    dirs = np.stack([nx, ny, nz], 1)
+    T = orc.OracleTables([orc.material(29, 0, 8.5e28, 0.0)], orc.table_spec(n_rows=96, n_cols=64))
+    tol = 2e-6                                    # float32 storage
+    for mask, g in ((orc.PROC_BREMS, 50.0), (orc.PROC_TRIDENT, 50.0)):
+        em, ion = _one_pair_per_cell(W, n, dirs * math.sqrt(g * g - 1))
+        sp = {"em": orc.OracleSpecies(em, cap=2 * n), "ep": orc.OracleSpecies(W.empty_species(), cap=1000),
+              "ph": orc.OracleSpecies(W.empty_species(), cap=1000), "ion": orc.OracleSpecies(ion)}
+        _, st = orc.step(T, n, np.zeros(n, np.int32), sp["em"], sp["ep"], sp["ph"], sp["ion"], 1e5, 1e-3, 5, 0,
+                         mask=mask)
+        assert st["rc"] == 0 and st["status"] == 2   # x > 1: every pair collides
+        e = sp["em"].as_dict()
+        prim = e["pid"] < (1 << 63)
+        ue = np.stack([e["ux"], e["uy"], e["uz"]], 1)[prim].astype(np.float64)
+        order = np.argsort(e["cell"][prim])
+        ue = ue[order]
+        assert np.allclose(_unit(ue), dirs, atol=tol)
+        ge = np.sqrt(1 + (ue ** 2).sum(1))
+        if mask == orc.PROC_BREMS:
+            assert st["created"][0] == n
+            p = sp["ph"].as_dict()
+            up = np.stack([p["ux"], p["uy"], p["uz"]], 1).astype(np.float64)[np.argsort(p["cell"])]
+            assert np.allclose(_unit(up), dirs, atol=tol)
+            assert np.allclose(ge + np.linalg.norm(up, axis=1), g, rtol=tol)
+        else:
+            assert st["created"][2] == n
+            sec = {k: sp[k].as_dict() for k in ("em", "ep")}
+            tot = ge.copy()
+            for k in ("em", "ep"):
+                d = sec[k]
+                m = d["pid"] >= (1 << 63)
+                u = np.stack([d["ux"], d["uy"], d["uz"]], 1).astype(np.float64)[m][np.argsort(d["cell"][m])]
+                assert len(u) == n
+                assert np.allclose(_unit(u), dirs, atol=tol)
+                tot += np.sqrt(1 + (u ** 2).sum(1))
+            assert np.allclose(tot, g, rtol=tol)
+    # Bethe-Heitler: photons of k = 30
+    k = 30.0
+    ph, ion = _one_pair_per_cell(W, n, dirs * k)
+    sp = {"em": orc.OracleSpecies(W.empty_species(), cap=1000), "ep": orc.OracleSpecies(W.empty_species(), cap=1000),
+          "ph": orc.OracleSpecies(ph), "ion": orc.OracleSpecies(ion)}
+    _, st = orc.step(T, n, np.zeros(n, np.int32), sp["em"], sp["ep"], sp["ph"], sp["ion"], 1e5, 1e-3, 5, 0,
+                     mask=orc.PROC_BH)
+    assert st["rc"] == 0 and st["status"] == 2
+    assert st["created"][4] == n and sp["ph"].n == 0
+    tot = np.zeros(n)
+    for key in ("em", "ep"):
+        d = sp[key].as_dict()
+        u = np.stack([d["ux"], d["uy"], d["uz"]], 1).astype(np.float64)[np.argsort(d["cell"])]
+        assert np.allclose(_unit(u), dirs, atol=tol)
+        tot += np.sqrt(1 + (u ** 2).sum(1))
+    assert np.allclose(tot, k, rtol=tol)
+
+
 @pytest.mark.slow
 def test_thin_target_yield_independent_of_weight_ratio(orc):
     """Fig. valid_brem_tf: a 40 MeV beam in neutral Cu (n_e = 1e21 cm^-3,
