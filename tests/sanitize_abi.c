@@ -1,12 +1,12 @@
 /*
- * Host-side driver for the C ABI of include/pcc.h, linked against a copy of
- * the library whose host code is built with AddressSanitizer and
- * UndefinedBehaviorSanitizer.  It needs no GPU: every call here must be
+ * Host-side test program for the C ABI of include/pcc.h, linked either
+ * against libpcc.so itself or against a copy of the library whose host code
+ * is built with AddressSanitizer and UndefinedBehaviorSanitizer (then any
+ * sanitizer report fails the run).  It needs no GPU: every call here must be
  * rejected by the library's own argument checks, before any CUDA work, with
  * the documented error code and a message in pcc_last_error().  A device
  * index that does not exist must fail in pcc_create with the output left
- * NULL.  Any out-of-bounds access, use of freed memory or undefined
- * behaviour in those paths aborts with a sanitizer report.
+ * NULL.
  */
 #include <stdint.h>
 #include <stdio.h>

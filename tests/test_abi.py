@@ -75,3 +75,24 @@ def test_status_strings_without_a_device(lib):
     assert pcc.status_bits(pcc.ST_TIMEOUT | pcc.ST_TABLE_RANGE) == ["PCC_ST_TABLE_RANGE", "PCC_ST_TIMEOUT"]
     with pytest.raises(pcc.PccError, match="PCC_E_INVALID"):
         pcc._check(L.pcc_create(None, 0), "pcc_create")
+
+
+def test_c_program_links_against_the_library(lib, tmp_path):
+    """A plain C program (the argument-check driver beside this file)
+    compiles against include/pcc.h with gcc, links libpcc.so and runs
+    without a GPU: the boundary is usable from C, not only through ctypes."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    from paper_1907_02814_gb300 import build
+    libdir = os.path.dirname(build.LIB)
+    exe = str(tmp_path / "abi_c")
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "sanitize_abi.c"), "-o", exe, "-L", libdir, "-l:libpcc.so",
+                        f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120,
+                       env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "all checks passed" in r.stdout
