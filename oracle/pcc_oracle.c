@@ -89,7 +89,10 @@ static double zeta_minus_one(double s)
 }
 
 /* Coulomb correction f_C(Z) of the ultra-relativistic Brems formula
- * (Sec. II.B.3), four terms of the zeta series (reading R2). */
+ * (Sec. II.B.3), four terms of the zeta series as the paper says.  The
+ * printed series starts at zeta(1), which diverges; it is read as the
+ * Davies-Bethe-Maximon form a^2 [1/(1+a^2) + sum_{n=0..3} (-a^2)^n
+ * (zeta(2n+3) - 1)], a = alpha Z. */
 double orc_fC(int Z)
 {
     double a2 = (ALPHA * Z) * (ALPHA * Z);
@@ -298,7 +301,10 @@ double orc_dsdk_brems_rel(const orc_screening *s, double gamma1, double k, doubl
     return v > 0.0 ? v : 0.0;
 }
 
-/* dsigma/dk in the ion rest frame, regime chosen by gamma1 (reading R6). */
+/* dsigma/dk in the ion rest frame, regime chosen by gamma1: the
+ * non-relativistic form up to 2, the relativistic one up to 100, the
+ * ultra-relativistic one above (the paper's ranges share their end points;
+ * the jumps there are kept). */
 double orc_dsdk_brems(const orc_screening *s, double gamma1, double k, int nr_qbounds)
 {
     if (gamma1 <= 2.0) return orc_dsdk_brems_nr(s, gamma1, k, nr_qbounds);
@@ -325,7 +331,7 @@ double orc_dsdg_bh(const orc_screening *s, double k, double gp)
 }
 
 /* Sec. II.D: Gryaznykh fit of the total Trident cross section, zero below
- * the pair threshold gamma1 = 3 (reading R12). */
+ * the pair threshold gamma1 = 3 (the fit itself turns negative below 2.39). */
 double orc_sigma_trident(int Z, double g1)
 {
     if (g1 < 3.0) return 0.0;
@@ -334,7 +340,9 @@ double orc_sigma_trident(int Z, double g1)
 }
 
 /* Sec. II.D: Bhabha low- and high-energy pair-energy spectra combined by
- * the product-over-sum interpolation (reading R11). */
+ * the product-over-sum interpolation.  Logs are natural; E_p is the pair's
+ * kinetic energy gamma_p - 2 in the low-energy form, so that the spectrum
+ * vanishes at threshold, and gamma_p in the high-energy form. */
 double orc_dsdgp_trident(int Z, double g1, double gp)
 {
     if (!(gp > 2.0 && gp < g1 - 1.0)) return 0.0;
@@ -559,7 +567,10 @@ double orc_sigma_lookup(const orc_table_spec *sp, const double *sig, double r, u
     return exp((1.0 - f) * log(sig[j]) + f * log(sig[j + 1]));
 }
 
-/* Inverse-CDF sample of the column variable (reading R10). */
+/* Inverse-CDF sample of the column variable: between the two rows around
+ * r, the upper one is taken when u_row is below r's fractional log position;
+ * then a binary search of that row's CDF and linear interpolation in the
+ * column's spacing variable (ln y for log-spaced columns, y otherwise). */
 double orc_sample(const orc_table_spec *sp, int table, const double *cdf, double r,
                   double u_row, double u_col)
 {
@@ -771,7 +782,8 @@ static int *canonical(const orc_species *sp, int n_cells, int **off_out)
 typedef struct { double E; double p[3]; } vec4;
 
 /* Lorentz transform of (E, p) into the rest frame of a particle with proper
- * velocity ui (Sec. III.A, reading R7):  E' = g E - ui.p,
+ * velocity ui (Sec. III.A; the printed last factor gamma_e beta_e is read as
+ * the ion's velocity, which makes the formula a boost):  E' = g E - ui.p,
  * p' = p + [ (ui.p)/(g+1) - E ] ui,  with g = sqrt(1 + ui^2). */
 static vec4 to_rest(vec4 a, const double ui[3], double gi)
 {

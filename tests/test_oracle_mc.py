@@ -93,10 +93,11 @@ def test_sampler_reproduces_row_cdf(orc, cu_tables):
 @pytest.mark.parametrize("table", ["TB_BREMS", "TB_BH", "TB_TRI_GP", "TB_TRI_SPLIT"])
 def test_sampler_mixes_neighbour_rows(orc, cu_tables, table):
     """Between rows j and j+1, at fractional log position f, the stochastic
-    row pick of reading R10 makes the samples follow (1-f) F_j + f F_{j+1},
-    each row's CDF interpolated linearly in the column's spacing variable
-    (ln y for the log-spaced Brems and Trident pair-energy columns, y for BH
-    and the split).  Checked by KS on every table kind."""
+    row pick (the upper row when u_row < f) makes the samples follow
+    (1-f) F_j + f F_{j+1}, each row's CDF interpolated linearly in the
+    column's spacing variable (ln y for the log-spaced Brems and Trident
+    pair-energy columns, y for BH and the split).  Checked by KS on every
+    table kind."""
     T = cu_tables
     tb = getattr(orc, table)
     arr = {"TB_BREMS": T.brems_cdf[1], "TB_BH": T.bh_cdf[1], "TB_TRI_GP": T.tri_gp_cdf,
@@ -180,7 +181,8 @@ def _run(orc, wl, steps, mask, spec=None, cap_extra=20000):
 @pytest.mark.parametrize("u_ion", [1.0, -1.0])
 def test_bh_rate_on_moving_ions_has_the_moller_flux(orc, u_ion):
     """Photons of k = 20 along +z on ions all moving along z with u = +-1
-    (readings R8, R9): the collision rate is n_g n_i sigma(k') c (1 - beta_i . n),
+    (Eq. proba3 with the photon's k, k' and c in place of the electron's
+    gamma, gamma' and v'): the collision rate is n_g n_i sigma(k') c (1 - beta_i . n),
     sigma at the Doppler-shifted ion-frame energy k' = k gamma_i (1 - beta_i . n)
     and the flux factor of a massless projectile on a moving target.
     Accepted events against that expectation, 4 sigma."""
@@ -213,7 +215,7 @@ def test_bh_rate_on_moving_ions_has_the_moller_flux(orc, u_ion):
 @pytest.mark.parametrize("ui", [(0.0, 0.0, 0.6), (0.0, 0.0, -0.6), (0.8, 0.0, 0.0)])
 def test_brems_rate_on_moving_ions_has_the_moller_flux(orc, ui):
     """Electrons of gamma = 20 along +z on ions all moving with momentum ui
-    (Eq. proba3 and reading R7): the collision rate is n_e n_i sigma(gamma')
+    (Eq. proba3 and the ion-frame transform of Sec. III.A): the collision rate is n_e n_i sigma(gamma')
     v_M with Moller's invariant flux v_M = sqrt(|v_e - v_i|^2 - |v_e x v_i|^2/c^2)
     written in lab velocities, and sigma at the ion-frame Lorentz factor
     gamma' = gamma_e gamma_i (1 - beta_e . beta_i).  4 sigma."""

@@ -446,7 +446,7 @@ def test_lorentz_transform(orc):
 
 
 def test_photon_doppler_shift(orc):
-    """Photons into the ion frame (reading R9): the relativistic Doppler
+    """Photons into the ion frame (Sec. III.A, BH variant): the relativistic Doppler
     shift k' = k gamma_i (1 - beta_i . n), a null vector stays null, and
     the aberrated direction obeys the textbook cos theta' =
     (cos theta - beta) / (1 - beta cos theta) about the ion velocity."""

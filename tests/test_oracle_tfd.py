@@ -134,7 +134,8 @@ def test_reduced_formula_stays_close_to_full_potential(orc, Zs, T):
 
 
 def test_regime_boundary_jumps(orc):
-    """The piecewise Brems model (reading R6) jumps at gamma1 = 2 (Eq. cs_br_nr
+    """The piecewise Brems model (non-relativistic up to 2, relativistic up
+    to 100, ultra-relativistic above) jumps at gamma1 = 2 (Eq. cs_br_nr
     with the Elwert factor below, Eq. csre above) and at gamma1 = 100
     (Eq. csur adds f_C).  The k-integrated cross sections on both sides,
     for both screening modes: about +190 % at gamma1 = 2 (the extreme-
