@@ -21,15 +21,16 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP contraction off, so x86 and Arm agree)."""
+    """Compile the oracle with gcc (FP contraction off, so x86 and Arm agree),
+    with OpenMP over cells for timing when the compiler has it."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "pcc_oracle.h"))
     ):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-             "-o", tmp, _SRC, "-lm"]
-        )
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -119,6 +120,13 @@ def lib():
             L.orc_boost.argtypes = [_dp, _dp, _dp, C.c_int]
             L.orc_expected_emission.argtypes = [C.POINTER(Material), C.c_int, _dp, _dp, C.c_int, _dp]
             L.orc_expected_emission_grad.argtypes = [C.POINTER(Material), C.c_int, _dp, _dp, C.c_int, _dp, _dp]
+            L.orc_expected_emission_grad_analytic.argtypes = [C.POINTER(Material), C.c_int, _dp, _dp, C.c_int,
+                                                              _dp, _dp]
+            L.orc_dI12_dL.argtypes = [d, d, _dp, _dp]
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_get_threads.restype = C.c_int
+            L.orc_dsdk_brems_grad.argtypes = [C.POINTER(Material), d, d, _dp]
+            L.orc_screening_jacobian.argtypes = [C.POINTER(Material), _dp]
     return _lib
 
 
@@ -338,6 +346,13 @@ class OracleSpecies:
         return {k: (v[order] if v is not None else None) for k, v in d.items()}
 
 
+def set_threads(n: int) -> int:
+    """Threads for the cells of a group in step() (timing only: the result
+    does not depend on it); returns the count in effect (1 without OpenMP)."""
+    lib().orc_set_threads(int(n))
+    return int(lib().orc_get_threads())
+
+
 def step(tables: OracleTables, n_cells, material_of_cell, em, ep, ph, ion, ion_mass, dt, seed,
          step_index, mask=PROC_BREMS | PROC_TRIDENT | PROC_BH, ledger=None):
     """One collision step; em/ep/ph are OracleSpecies updated in place."""
@@ -383,3 +398,35 @@ def expected_emission_grad(mat: Material, gamma, w, g_out, n_quad=64):
                                      int(n_quad), go.ctypes.data_as(_dp), out.ctypes.data_as(_dp))
     return out
 
+
+
+def expected_emission_grad_analytic(mat: Material, gamma, w, g_out, n_quad=64):
+    """sum_j g_out[j] d out[j] / d (n_i, T_e, Z*, s_TF, s_D) by the chain rule
+    written out by hand (FP64)."""
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    go = np.ascontiguousarray(g_out, dtype=np.float64)
+    out = np.zeros(5)
+    lib().orc_expected_emission_grad_analytic(C.byref(mat), len(g), g.ctypes.data_as(_dp), ww.ctypes.data_as(_dp),
+                                              int(n_quad), go.ctypes.data_as(_dp), out.ctypes.data_as(_dp))
+    return out
+
+
+def dI12_dL(delta, L):
+    a, b = C.c_double(), C.c_double()
+    lib().orc_dI12_dL(float(delta), float(L), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def dsdk_brems_grad(mat: Material, gamma1, k):
+    """d(dsigma/dk)/d(L_TF, L_D, eta_D, L_R)."""
+    out = np.zeros(4)
+    lib().orc_dsdk_brems_grad(C.byref(mat), float(gamma1), float(k), out.ctypes.data_as(_dp))
+    return out
+
+
+def screening_jacobian(mat: Material):
+    """d(L_TF, L_D, eta_D, L_R)/d(n_i, T_e, Z*, s_TF, s_D) as a 4 x 5 array."""
+    out = np.zeros(20)
+    lib().orc_screening_jacobian(C.byref(mat), out.ctypes.data_as(_dp))
+    return out.reshape(4, 5)

@@ -27,6 +27,9 @@
  *       with the counter layout documented at orc_step().
  */
 #include "pcc_oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include <math.h>
 #include <stdlib.h>
@@ -816,10 +819,17 @@ void orc_boost(const double ui[3], const double in[4], double out[4], int invers
     out[0] = b.E; out[1] = b.p[0]; out[2] = b.p[1]; out[3] = b.p[2];
 }
 
+/* Append one particle.  Under OpenMP the slot is taken with an atomic
+ * increment (cells run on several threads); a slot past the capacity is
+ * refused and the count is clamped back after the group (orc_step). */
 static int append(orc_species *sp, const double u[3], double w, float x, int has_x, uint64_t pid, int cell)
 {
-    if (sp->n >= sp->cap) return 1;
-    int i = sp->n++;
+    int i;
+#ifdef _OPENMP
+#pragma omp atomic capture
+#endif
+    i = sp->n++;
+    if (i >= sp->cap) return 1;
     sp->ux[i] = (float)u[0]; sp->uy[i] = (float)u[1]; sp->uz[i] = (float)u[2];
     sp->w[i] = (float)w;
     if (sp->x && has_x) sp->x[i] = x;
@@ -1011,6 +1021,27 @@ static void pair_of(uint32_t j, uint32_t Np, uint32_t Nt, const uint32_t rk[4], 
  *   event draws:       (j,      cell, step, group | EVT<<4)
  * with U = ((r >> 9) + 1/2) 2^-23 for the event draws.
  */
+static int g_threads = 1;
+
+/* Threads for the cells of one group in orc_step (timing only; the result
+ * does not depend on it).  1 without OpenMP. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+}
+
+int orc_get_threads(void) { return g_threads; }
+
+static void clamp_count(orc_species *sp)
+{
+    if (sp->n > sp->cap) sp->n = sp->cap;
+}
+
 int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
              orc_species *em, orc_species *ep, orc_species *ph, const orc_species *ion,
              double ion_mass, double dt, uint64_t seed, uint64_t step, unsigned mask,
@@ -1025,12 +1056,34 @@ int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
     for (int g = 0; g < 3; ++g) { idx_g[g] = canonical(proj[g], n_cells, &off_g[g]); n0[g] = proj[g]->n; }
     int err = 0;
     unsigned char *dead = calloc(ph->n > 0 ? ph->n : 1, 1);
+    /* per-thread counters, merged after each group (integer-valued sums, so
+     * the merge order does not matter) */
+    int nth = g_threads;
+    orc_stats *tst = calloc((size_t)nth, sizeof(orc_stats));
 
     for (int g = 0; g < 3 && !err; ++g) {
         if (g < 2 && !(mask & (ORC_PROC_BREMS | ORC_PROC_TRIDENT))) continue;
         if (g == 2 && !(mask & ORC_PROC_BH)) continue;
         orc_species *P = proj[g];
-        for (int cell = 0; cell < n_cells && !err; ++cell) {
+        /* cells are independent within a group: a cell touches only its own
+         * projectiles, ledger entry and absorbed-photon flags, and appends
+         * secondaries through atomically taken slots */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nth)
+#endif
+        for (int cell = 0; cell < n_cells; ++cell) {
+            int stop;
+#ifdef _OPENMP
+#pragma omp atomic read
+#endif
+            stop = err;
+            if (stop) continue;
+#ifdef _OPENMP
+            orc_stats *mst = &tst[omp_get_thread_num()];
+#else
+            orc_stats *mst = &tst[0];
+#endif
+            int cerr = 0;
             uint32_t Np = off_g[g][cell + 1] - off_g[g][cell];
             uint32_t Nt = off_i[cell + 1] - off_i[cell];
             if (Np == 0 || Nt == 0) continue;
@@ -1047,7 +1100,7 @@ int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
                 pair_of(j, Np, Nt, rk, &s, &tau);
                 n_pt += fmin((double)P->w[pidx[s]], (double)ion->w[tidx[tau]]);
             }
-            st->pairs[g] += Npair;
+            mst->pairs[g] += Npair;
             pair_ctx c;
             c.t = t;
             c.mat = material_of_cell[cell];
@@ -1055,8 +1108,8 @@ int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
             c.ion_mass = ion_mass;
             c.coef = n_p * n_t / n_pt * C_LIGHT * dt;
             c.seed = seed; c.step = step; c.cell = (uint32_t)cell;
-            c.ledger = ledger; c.st = st;
-            for (uint32_t j = 0; j < Npair && !err; ++j) {
+            c.ledger = ledger; c.st = mst;
+            for (uint32_t j = 0; j < Npair && !cerr; ++j) {
                 uint32_t s, tau;
                 pair_of(j, Np, Nt, rk, &s, &tau);
                 uint32_t m = Np >= Nt ? 0 : j / Np;
@@ -1068,16 +1121,31 @@ int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
                 int ip = pidx[s], it = tidx[tau];
                 if (g < 2) {
                     if (mask & ORC_PROC_BREMS)
-                        err |= brems_pair(&c, g, P, ip, ion, it, j, acc[2 * (s & 1)], &s1, ph);
+                        cerr |= brems_pair(&c, g, P, ip, ion, it, j, acc[2 * (s & 1)], &s1, ph);
                     if (mask & ORC_PROC_TRIDENT)
-                        err |= trident_pair(&c, g, P, ip, ion, it, j, acc[2 * (s & 1) + 1], &s2, em, ep);
+                        cerr |= trident_pair(&c, g, P, ip, ion, it, j, acc[2 * (s & 1) + 1], &s2, em, ep);
                 } else {
                     if (dead[ip]) continue;
-                    if (bh_pair(&c, P, ip, ion, it, j, acc[2 * (s & 1)], &s1, em, ep, &err)) dead[ip] = 1;
+                    if (bh_pair(&c, P, ip, ion, it, j, acc[2 * (s & 1)], &s1, em, ep, &cerr)) dead[ip] = 1;
                 }
             }
+            if (cerr) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                err = 1;
+            }
         }
+        clamp_count(em);
+        clamp_count(ep);
+        clamp_count(ph);
     }
+    for (int k = 0; k < nth; ++k) {
+        for (int g = 0; g < 3; ++g) st->pairs[g] += tst[k].pairs[g];
+        for (int ch = 0; ch < 5; ++ch) { st->accepted[ch] += tst[k].accepted[ch]; st->created[ch] += tst[k].created[ch]; }
+        st->status |= tst[k].status;
+    }
+    free(tst);
     /* remove absorbed photons, keeping the order of the rest */
     int w = 0;
     for (int i = 0; i < ph->n; ++i) {
@@ -1164,3 +1232,282 @@ void orc_expected_emission_grad(const orc_material *m, int n_samples, const doub
     }
 }
 
+
+/* ------------------------------------------------------------------------ */
+/* Analytic gradient of the expected-emission operator                       */
+/* ------------------------------------------------------------------------ */
+
+/* Derivatives with respect to L of the single-Yukawa screening functions of
+ * Eqs. (deriv_I1) and (deriv_I2), by differentiating each term by hand:
+ *   dI1/dL = d (atan dL - atan L) + L (1-d)/(1+L^2) - L (1-d)^2/(1+L^2)^2,
+ *   d(2 I2)/dL = 12 L^2 d^3 (atan dL - atan L) + 4 L^3 d^3 (d/(1+L^2 d^2) - 1/(1+L^2))
+ *              + 6 L d^2 ln((1+L^2)/(1+L^2 d^2)) + (1 + 3 L^2 d^2)(2L/(1+L^2) - 2 L d^2/(1+L^2 d^2))
+ *              + 12 d^2 ln d  L^3 (L^2+2)/(1+L^2)^2
+ *              + (d-1)(2L(d+1) - 16 L^3 d^2 - 8 L^5 d^2)/(1+L^2)^2.
+ * atan dL - atan L is formed as atan((dL - L)/(1 + d L^2)).  Where delta L > 4
+ * these terms (those of d(2 I2)/dL of order L (delta L)^2) cancel down to
+ * O(1/(delta^2 L^3)); there both derivatives are taken from their integral
+ * definitions (dI12_dL_quad) instead. */
+static void dI12_dL_quad(double d, double L, double *dI1, double *dI2);
+
+void orc_dI12_dL(double d, double L, double *dI1, double *dI2)
+{
+    double L2 = L * L, d2 = d * d, u2 = L2 * d2;
+    double q = 1.0 + L2;
+    if (d * L > 4.0) {
+        /* the terms below cancel to O(1/(d^2 L^3)) */
+        dI12_dL_quad(d, L, dI1, dI2);
+        return;
+    }
+    double dat = atan((d * L - L) / (1.0 + d * L2));
+    *dI1 = d * dat + L * (1.0 - d) / q - L * (1.0 - d) * (1.0 - d) / (q * q);
+    double t1 = 12.0 * L2 * d2 * d * dat + 4.0 * L2 * L * d2 * d * (d / (1.0 + u2) - 1.0 / q);
+    double t2 = 6.0 * L * d2 * log(q / (1.0 + u2)) + (1.0 + 3.0 * u2) * (2.0 * L / q - 2.0 * L * d2 / (1.0 + u2));
+    double t3 = 12.0 * d2 * log(d) * L2 * L * (L2 + 2.0) / (q * q);
+    double t4 = (d - 1.0) * (2.0 * L * (d + 1.0) - 16.0 * L2 * L * d2 - 8.0 * L2 * L2 * L * d2) / (q * q);
+    *dI2 = 0.5 * (t1 + t2 + t3 + t4);
+}
+
+/* d I1/dL and d I2/dL from the integral definitions (Eqs. defphi1, defphi2)
+ * for the single-Yukawa form factor 1 - F = (L u)^2/(1 + (L u)^2) of Eq.
+ * (defF): with t = ln u and r = u/delta,
+ *   dI1/dL = int_{ln delta}^0 (1 - 1/r)^2 d(1-F)^2/dL dt,
+ *   dI2/dL = int_{ln delta}^0 [1 + (3 - 6 ln r)/r^2 - 4/r^3] d(1-F)^2/dL dt,
+ * d(1-F)^2/dL = 4 L^3 u^4/(1 + L^2 u^2)^3; composite 8-point Gauss-Legendre
+ * on equal panels no wider than 1/2.  Used where delta L > 4, where the
+ * closed forms lose their digits to cancellation. */
+static void dI12_dL_quad(double d, double L, double *dI1, double *dI2)
+{
+    double gx[8], gw[8];
+    orc_gauss_legendre(8, gx, gw);
+    double t0 = log(d);
+    int n = (int)ceil(-t0 / 0.5);
+    double h = -t0 / n, s1 = 0.0, s2 = 0.0;
+    for (int p = 0; p < n; ++p) {
+        double mid = t0 + (p + 0.5) * h;
+        for (int q = 0; q < 8; ++q) {
+            double t = mid + 0.5 * h * gx[q];
+            double lr = t - t0, r = exp(lr), u = exp(t), Lu2 = L * L * u * u;
+            double a = -expm1(-lr);
+            double k2 = 1.0 + (3.0 - 6.0 * lr) / (r * r) - 4.0 / (r * r * r);
+            double dF2 = 4.0 * L * L * L * u * u * u * u / ((1.0 + Lu2) * (1.0 + Lu2) * (1.0 + Lu2));
+            s1 += gw[q] * a * a * dF2;
+            s2 += gw[q] * k2 * dF2;
+        }
+    }
+    *dI1 = 0.5 * h * s1;
+    *dI2 = 0.5 * h * s2;
+}
+
+/* The two functions that enter a cross term K(A, B) = (B f(A) - A f(B))/(B - A):
+ * kind 0: f(t) = ln(1 + t) (Eq. ITFD); kind 1: f(t) = ln((1 + p t)/(1 + m t))
+ * (Gamma_c of Eq. cs_br_nr, p = dp+^2, m = dp-^2).  Value and two derivatives. */
+static void cross_f(int kind, double p, double m, double t, double *f, double *f1, double *f2)
+{
+    if (kind == 0) {
+        *f = log1p(t);
+        *f1 = 1.0 / (1.0 + t);
+        *f2 = -1.0 / ((1.0 + t) * (1.0 + t));
+    } else {
+        double P = 1.0 + p * t, M = 1.0 + m * t;
+        *f = log(P / M);
+        *f1 = p / P - m / M;
+        *f2 = -p * p / (P * P) + m * m / (M * M);
+    }
+}
+
+/* K(A, B) = (B f(A) - A f(B))/(B - A) and its partial derivatives.  Far from
+ * A = B directly: K_A = (B f'(A) - f(B) + K)/(B - A), K_B = (f(A) - A f'(B) - K)/(B - A).
+ * Near A = B (|B - A| <= B/10) through the divided difference of chi(t) = f(t)/t:
+ * K = -A B chi[A, B] with chi[A, B] = int_0^1 chi'(A + s(B - A)) ds, and
+ * d chi[A,B]/dA = int_0^1 (1 - s) chi''(.) ds, d chi[A,B]/dB = int_0^1 s chi''(.) ds,
+ * by 8-point Gauss-Legendre in s (chi is analytic on a disk much wider than
+ * the interval, so the rule is exact to rounding). */
+static void cross_partials(int kind, double p, double m, double A, double B, double *K, double *KA, double *KB)
+{
+    double D = B - A;
+    if (fabs(D) > 0.1 * fmax(A, B)) {
+        double fA, fA1, fA2, fB, fB1, fB2;
+        cross_f(kind, p, m, A, &fA, &fA1, &fA2);
+        cross_f(kind, p, m, B, &fB, &fB1, &fB2);
+        *K = (B * fA - A * fB) / D;
+        *KA = (B * fA1 - fB + *K) / D;
+        *KB = (fA - A * fB1 - *K) / D;
+        return;
+    }
+    double gx[8], gw[8];
+    orc_gauss_legendre(8, gx, gw);
+    double J0 = 0.0, JA = 0.0, JB = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        double s = 0.5 * (gx[q] + 1.0), w = 0.5 * gw[q];
+        double t = A + s * D, f, f1, f2;
+        cross_f(kind, p, m, t, &f, &f1, &f2);
+        double c1 = f1 / t - f / (t * t);
+        double c2 = f2 / t - 2.0 * f1 / (t * t) + 2.0 * f / (t * t * t);
+        J0 += w * c1;
+        JA += w * (1.0 - s) * c2;
+        JB += w * s * c2;
+    }
+    *K = -A * B * J0;
+    *KA = -B * J0 - A * B * JA;
+    *KB = -A * J0 - A * B * JB;
+}
+
+/* Jacobian J[i][k] = d S_i / d theta_k of the screening quantities
+ * S = (L_TF, L_D, eta_D, L_R) with respect to theta = (n_i, T_e, Z*, s_TF, s_D):
+ *   L_TF = s_TF Z^(-1/3)/alpha (Eq. LTF);
+ *   L_D = s_D max(lambda_D, r_i)/r_C (Eq. LDH), the active branch's derivative
+ *     (r_i on a tie), lambda_D^2 = eps0 T_e/(e n_i Z*(Z*+1)), r_i^3 = 3/(4 pi n_i);
+ *   eta_D = Zs/Z with Zs = Z^*, eta_TF = 1 - eta_D (Eq. V_TFD);
+ *   a = I_TFD (Eq. ITFD); L_R^2 = x solves h(x) = ln(1+x) - x/(1+x) = 2a
+ *     (Eq. reduit), so dL_R/da = (1/(2 L_R)) 2/h'(x) = (1+x)^2/(x L_R).
+ * At Z* = 0, Eq. LDH gives lambda_D = infinity: the operator does not depend
+ * on L_D there (eta_D = 0), and the derivative with respect to Z* is the
+ * limit from Z* > 0, in which the cross terms tend to their B -> infinity
+ * values (ln(1+A) for I_TFD) and every path through L_D vanishes. */
+static void screening_jacobian(const orc_material *m, const orc_screening *s, double J[4][5])
+{
+    memset(J, 0, sizeof(double) * 20);
+    double Z = m->Z, Zs = m->Zstar;
+    int inf_debye = !(Zs > 0.0);
+    J[0][3] = s->LTF / m->s_TF;
+    if (!inf_debye) {
+        if (s->lambdaD > s->ri) {
+            J[1][0] = -0.5 * s->LD / m->n_i;
+            J[1][1] = 0.5 * s->LD / m->T_e;
+            J[1][2] = -0.5 * s->LD * (2.0 * Zs + 1.0) / (Zs * (Zs + 1.0));
+        } else {
+            J[1][0] = -s->LD / (3.0 * m->n_i);
+        }
+        J[1][4] = s->LD / m->s_D;
+    }
+    J[2][2] = 1.0 / Z;
+    double A = s->LTF * s->LTF, B = s->LD * s->LD;
+    double eT = s->etaTF, eD = s->etaD;
+    double gA = log1p(A) - A / (1.0 + A), g1A = A / ((1.0 + A) * (1.0 + A));
+    double gB = log1p(B) - B / (1.0 + B), g1B = B / ((1.0 + B) * (1.0 + B));
+    double C, CA, CB;
+    if (inf_debye) { C = log1p(A); CA = 1.0 / (1.0 + A); CB = 0.0; gB = 0.0; g1B = 0.0; }
+    else cross_partials(0, 0.0, 0.0, A, B, &C, &CA, &CB);
+    double a_LTF = (0.5 * eT * eT * g1A + eT * eD * CA) * 2.0 * s->LTF;
+    double a_LD = inf_debye ? 0.0 : (0.5 * eD * eD * g1B + eT * eD * CB) * 2.0 * s->LD;
+    double a_eD = -eT * gA + eD * gB + (eT - eD) * C;
+    double x = s->LR * s->LR;
+    double LR_a = (1.0 + x) * (1.0 + x) / (x * s->LR);
+    for (int k = 0; k < 5; ++k)
+        J[3][k] = LR_a * (a_LTF * J[0][k] + a_LD * J[1][k] + a_eD * J[2][k]);
+}
+
+/* Partial derivatives of dsigma/dk (orc_dsdk_brems with exact NR bounds)
+ * with respect to S = (L_TF, L_D, eta_D, L_R) at fixed Z and energies; zero
+ * where the cross section is clamped at zero.  inf_debye: L_D = infinity
+ * (Z* = 0). */
+static void dsdk_brems_partials(const orc_screening *s, double gamma1, double k, int inf_debye, double out[4])
+{
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    double T1 = gamma1 - 1.0;
+    if (!(k > 0.0 && k < T1)) return;
+    if (orc_dsdk_brems(s, gamma1, k, ORC_NR_EXACT) <= 0.0) return;
+    double Z = s->Z;
+    if (gamma1 <= 2.0) {
+        double T2 = T1 - k;
+        double p1 = sqrt(T1 * (T1 + 2.0)), p2 = sqrt(T2 * (T2 + 2.0));
+        double dpp = p1 + p2, dpm = k * (T1 + T2 + 2.0) / (p1 + p2);
+        double b1 = p1 / gamma1, b2 = p2 / (1.0 + T2), az = 2.0 * PI * Z * ALPHA;
+        double fE = (b1 / b2) * (-expm1(-az / b1)) / (-expm1(-az / b2));
+        double pre = 16.0 * R_E * R_E * Z * Z * ALPHA / (3.0 * k * p1 * p1) * fE;
+        double pp = dpp * dpp, mm = dpm * dpm;
+        /* g(eta, L) = eta^2/2 [ln(D+/D-) + 1/D+ - 1/D-], D+- = dp+-^2 L^2 + 1:
+         * dg/deta = eta [..], dg/dL = eta^2 L^3 (dp+^4/D+^2 - dp-^4/D-^2) */
+        double LT = s->LTF, LTa = LT * LT;
+        double Dp = pp * LTa + 1.0, Dm = mm * LTa + 1.0;
+        double brT = log(Dp / Dm) + 1.0 / Dp - 1.0 / Dm;
+        double gT_L = s->etaTF * s->etaTF * LTa * LT * (pp * pp / (Dp * Dp) - mm * mm / (Dm * Dm));
+        double gT_eta = s->etaTF * brT;
+        double gD_L = 0.0, gD_eta = 0.0;
+        if (!inf_debye) {
+            double LD = s->LD, LDa = LD * LD;
+            double Ep = pp * LDa + 1.0, Em = mm * LDa + 1.0;
+            gD_L = s->etaD * s->etaD * LDa * LD * (pp * pp / (Ep * Ep) - mm * mm / (Em * Em));
+            gD_eta = s->etaD * (log(Ep / Em) + 1.0 / Ep - 1.0 / Em);
+        }
+        /* Gamma_c = eta_TF eta_D K(A, B), K(A, B) = (B psi(A) - A psi(B))/(B - A) */
+        double K, KA, KB;
+        if (inf_debye) {
+            double f, f1, f2;
+            cross_f(1, pp, mm, LTa, &f, &f1, &f2);
+            K = f; KA = f1; KB = 0.0;
+        } else {
+            cross_partials(1, pp, mm, LTa, s->LD * s->LD, &K, &KA, &KB);
+        }
+        double eT = s->etaTF, eD = s->etaD;
+        out[0] = pre * (gT_L + eT * eD * KA * 2.0 * LT);
+        out[1] = inf_debye ? 0.0 : pre * (gD_L + eT * eD * KB * 2.0 * s->LD);
+        out[2] = pre * (-gT_eta + gD_eta + (eT - eD) * K);
+        return;
+    }
+    /* relativistic regimes: f_C does not depend on theta */
+    double eps = (gamma1 - k) / gamma1;
+    double delta = k / (2.0 * gamma1 * (gamma1 - k));
+    double dI1, dI2;
+    orc_dI12_dL(delta, s->LR, &dI1, &dI2);
+    out[3] = 4.0 * Z * Z * R_E * R_E * ALPHA / k * ((1.0 + eps * eps) * dI1 - 2.0 / 3.0 * eps * dI2);
+}
+
+/* Exported for the tests: d(dsigma/dk)/d(L_TF, L_D, eta_D, L_R) and the
+ * screening Jacobian d(L_TF, L_D, eta_D, L_R)/d(n_i, T_e, Z*, s_TF, s_D). */
+void orc_dsdk_brems_grad(const orc_material *m, double gamma1, double k, double out4[4])
+{
+    orc_screening s;
+    orc_screening_prep(m, &s);
+    dsdk_brems_partials(&s, gamma1, k, !(m->Zstar > 0.0), out4);
+}
+
+void orc_screening_jacobian(const orc_material *m, double jac20[20])
+{
+    orc_screening s;
+    orc_screening_prep(m, &s);
+    double J[4][5];
+    screening_jacobian(m, &s, J);
+    memcpy(jac20, J, sizeof J);
+}
+
+/* Gradient of the expected-emission operator, contracted with g_out, by the
+ * chain rule written out by hand (no differencing):
+ *   d out_j/d theta_k = [k = n_i] out_j/n_i
+ *     + n_i sum_s w_s v_s sum_q h w_q T x (x T)^[j=2] sum_i d(dsigma/dk)/dS_i J[i][k]
+ * for j = 0 (photons) and 2 (power); the pair rate (j = 1) depends on theta
+ * through n_i only.  Same quadrature as orc_expected_emission. */
+void orc_expected_emission_grad_analytic(const orc_material *m, int n_samples, const double *gamma,
+                                         const double *w, int n_quad, const double *g_out, double *grad)
+{
+    orc_screening s;
+    orc_screening_prep(m, &s);
+    double J[4][5];
+    screening_jacobian(m, &s, J);
+    int inf_debye = !(m->Zstar > 0.0);
+    double gx[128], gw[128];
+    if (n_quad > 128) n_quad = 128;
+    orc_gauss_legendre(n_quad, gx, gw);
+    double a = log(1e-7), b = 0.0, h = 0.5 * (b - a), mid = 0.5 * (a + b);
+    double dS[4] = { 0.0, 0.0, 0.0, 0.0 };   /* d(g0 R + g2 P)/dS / n_i */
+    double out3[3];
+    orc_expected_emission(m, n_samples, gamma, w, n_quad, out3);
+    for (int i = 0; i < n_samples; ++i) {
+        double g = gamma[i], T = g - 1.0;
+        double v = C_LIGHT * sqrt(T * (T + 2.0)) / g;
+        for (int q = 0; q < n_quad; ++q) {
+            double x = exp(mid + h * gx[q]);
+            double part[4];
+            dsdk_brems_partials(&s, g, x * T, inf_debye, part);
+            double c = w[i] * v * h * gw[q] * T * x * (g_out[0] + g_out[2] * x * T);
+            for (int r = 0; r < 4; ++r) dS[r] += c * part[r];
+        }
+    }
+    for (int k = 0; k < 5; ++k) {
+        double acc = 0.0;
+        for (int r = 0; r < 4; ++r) acc += dS[r] * J[r][k];
+        grad[k] = m->n_i * acc;
+    }
+    grad[0] += (g_out[0] * out3[0] + g_out[1] * out3[1] + g_out[2] * out3[2]) / m->n_i;
+}

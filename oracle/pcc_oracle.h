@@ -8,7 +8,10 @@
  * header, helper or constant generator with the CUDA library; the two are
  * written independently from the paper and compared value by value.
  *
- * Everything here is plain, slow, single-threaded C in double precision.
+ * Everything here is plain, slow C in double precision, single-threaded
+ * unless orc_set_threads asks for OpenMP threads over the cells of a group
+ * (for timing the CPU baseline; cells are independent, so the result is the
+ * same).
  * Particle state is held in the same storage format as the product
  * (float32 momenta and weights, uint64 ids); all arithmetic is FP64.
  *
@@ -133,6 +136,10 @@ double orc_sample(const orc_table_spec *sp, int table, const double *cdf, double
 void orc_boost(const double ui[3], const double in[4], double out[4], int inverse);
 
 /* ---- the collision step (Sec. III.A) ---- */
+/* Threads over the cells of a group (OpenMP builds only; timing only, the
+ * result does not depend on it).  Default 1. */
+void orc_set_threads(int n);
+int  orc_get_threads(void);
 int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
              orc_species *em, orc_species *ep, orc_species *ph, const orc_species *ion,
              double ion_mass, double dt, uint64_t seed, uint64_t step, unsigned mask,
@@ -143,6 +150,16 @@ void orc_expected_emission(const orc_material *m, int n_samples, const double *g
                            const double *w, int n_quad, double *out3);
 void orc_expected_emission_grad(const orc_material *m, int n_samples, const double *gamma,
                                 const double *w, int n_quad, const double *g_out, double *grad5);
+/* The same gradient by the chain rule written out by hand: d/dL of the
+ * reduced screening functions, the partials of I_TFD and of the NR cross
+ * term, the implicit Lambert-W derivative dL_R/da, and the Jacobian of
+ * (L_TF, L_D, eta_D, L_R) with respect to theta.  At Z* = 0 the Z*
+ * derivative is the limit from Z* > 0 (lambda_D -> infinity). */
+void orc_expected_emission_grad_analytic(const orc_material *m, int n_samples, const double *gamma,
+                                         const double *w, int n_quad, const double *g_out, double *grad5);
+void orc_dI12_dL(double delta, double L, double *dI1, double *dI2);
+void orc_dsdk_brems_grad(const orc_material *m, double gamma1, double k, double out4[4]);
+void orc_screening_jacobian(const orc_material *m, double jac20[20]);
 
 #ifdef __cplusplus
 }

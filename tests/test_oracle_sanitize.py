@@ -23,9 +23,11 @@ SRC = [os.path.join(HERE, "sanitize_oracle.c"), os.path.join(ORACLE, "pcc_oracle
 pytestmark = pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
 
 
-def test_oracle_compiles_without_warnings(tmp_path):
+@pytest.mark.parametrize("openmp", [False, True])
+def test_oracle_compiles_without_warnings(tmp_path, openmp):
     r = subprocess.run(["gcc", "-std=c11", "-O2", "-Wall", "-Wextra", "-Werror", "-ffp-contract=off",
-                        "-fsyntax-only", "-I", ORACLE] + SRC, capture_output=True, text=True)
+                        "-fsyntax-only", "-I", ORACLE] + (["-fopenmp"] if openmp else []) + SRC,
+                       capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
 
 
