@@ -324,7 +324,8 @@ def run_gpu(args):
     e2e = e2e_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, seed, prec)
     plain = plain_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, seed, ledger,
                           pairs_all / args.steps / world) if prec == pcc.FP32_BATCHED and args.plain_steps > 0 else None
-    emission = emission_measure(ctx, pcc, torch, W) if not args.no_emission else None
+    emission = emission_measure(ctx, pcc, torch, W, local) if not args.no_emission else None
+    config2 = config2_measure(ctx, pcc, torch, W) if not args.no_config2 else None
 
     peak, peak_kind = peaks()
     K = args.steps
@@ -365,6 +366,7 @@ def run_gpu(args):
         "e2e": e2e,
         "plain_fp64": plain and dict(plain, speedup_of_batched=plain["ms_per_step"] / (ms_max / K)),
         "expected_emission": emission,
+        "config2": config2,
         "gpu_launches": int(launches),
         "clocks": clk,
         "status": status,
@@ -400,9 +402,47 @@ def plain_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt
             "status": status}
 
 
-def emission_measure(ctx, pcc, torch, W, reps=5):
+# Sources of the expected-emission kernels: the ncu summary's instruction
+# counts are used only while its hash still matches.
+EMISSION_SOURCES = ("pcc_emission.cu", "pcc_physics.cuh", "pcc_internal.h", "pcc_device.cuh")
+EMISSION_PROFILE = "expected_emission_4096x512_full.md"
+SM_LANES = 128          # FP32 lanes (and thread-instructions issued per clock) per SM
+
+
+def emission_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1907_02814_gb300", "csrc")
+    for f in EMISSION_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def emission_instructions():
+    """Warp instructions per launch of the forward and adjoint emission
+    kernels from the committed ncu summary, if it was taken on the current
+    sources (else None)."""
+    p = os.path.join(ROOT, "profiles", EMISSION_PROFILE)
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    if f"source_hash: {emission_source_hash()}" not in text:
+        return None
+    out, which = {}, None
+    for line in text.splitlines():
+        if line.startswith("## ") and "emission_kernel<0>" in line:
+            which = "fwd"
+        elif line.startswith("## ") and "emission_kernel<1>" in line:
+            which = "bwd"
+        elif which and line.startswith("- warp instructions:"):
+            out[which] = float(line.split(":")[1].split()[0])
+    return out if len(out) == 2 else None
+
+
+def emission_measure(ctx, pcc, torch, W, local=0, reps=5):
     """Expected-emission operator at 4096 cells x 512 samples x 64 nodes:
-    forward and adjoint kernel times (CUDA events, median of reps)."""
+    forward and adjoint kernel times (CUDA events, median of reps), and the
+    issue roofline: warp instructions per launch (ncu) x 32 over the time,
+    against SMs x 128 thread-instructions per clock at the sampled SM clock."""
     d = W.emission_params()
     params = torch.as_tensor(np.stack([d[k] for k in ("n_i", "T_e", "Zstar", "s_TF", "s_D")], 1),
                              dtype=torch.float32, device="cuda")
@@ -411,6 +451,8 @@ def emission_measure(ctx, pcc, torch, W, reps=5):
     gout = torch.ones((g.shape[0], 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     res = {}
+    clocks = ClockSampler(local)
+    clocks.start()
     for name, fn in (("fwd", lambda: pcc.expected_emission_fwd(ctx, d["Z"], params, g, w)),
                      ("bwd", lambda: pcc.expected_emission_bwd(ctx, d["Z"], params, g, w, gout))):
         fn()
@@ -423,11 +465,86 @@ def emission_measure(ctx, pcc, torch, W, reps=5):
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
         res[f"ms_{name}"] = float(np.median(ms))
+    clk = clocks.stop()
     samples = g.numel()
     res.update({"cells": g.shape[0], "samples": samples, "nodes": 64,
                 "fwd_samples_per_s": samples / (res["ms_fwd"] * 1e-3),
-                "bwd_samples_per_s": samples / (res["ms_bwd"] * 1e-3)})
+                "bwd_samples_per_s": samples / (res["ms_bwd"] * 1e-3), "clocks": clk})
+    inst = emission_instructions()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clk["sm_mhz"] or clk["sm_max_mhz"]
+    if inst and mhz:
+        peak = sms * SM_LANES * mhz * 1e6 / 1e12
+        res["roofline"] = {}
+        for name in ("fwd", "bwd"):
+            ach = inst[name] * 32 / (res[f"ms_{name}"] * 1e-3) / 1e12
+            res["roofline"][name] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T thread-instr/s",
+                                     "frac": ach / peak, "thread_instr_per_node":
+                                         inst[name] * 32 / (samples * 64)}
     ctx.read_status()
+    return res
+
+
+def config2_measure(ctx, pcc, torch, W, steps=100, plain_steps=3):
+    """The Au foil configuration (16384 cells, Poisson(256) electrons per cell,
+    E^-2 on 0.1-100 MeV, 64 Au ions per cell with integer Z* in [10, 40]: 31
+    material tables, 256 x 256, built in FP64), Brems + Bethe-Heitler, dt =
+    1 fs: `steps` steps of collide + commit as one CUDA graph on the batched
+    FP32 path, and eager steps of the plain FP64 path from the same initial
+    state.  Particles are not moved between steps (the push of the transport
+    run is a harness, not part of the collision step)."""
+    wl = W.au_foil()
+    ctx.tables_build([pcc.material(m.Z, m.Zstar, m.n_i, m.T_e) for m in wl.materials], pcc.table_spec())
+    mat = torch.as_tensor(wl.material_of_cell, device="cuda")
+    n_cells = wl.n_cells
+    mask = pcc.BREMS | pcc.BH
+    slack = {"em": 16, "ep": 16, "ph": 128, "ion": 0}
+    empty = {"n": 0, "ux": None, "uy": None, "uz": None, "w": None, "pid": None, "cell": None, "x": None}
+
+    def state():
+        dev = {}
+        for k, d in wl.species.items():
+            n = len(d["w"])
+            sp = pcc.DeviceSpecies.empty(n_cells, n + (slack[k] + 1) * n_cells, with_x=d.get("x") is not None)
+            pcc.bin(ctx, pcc.particles_to_device(d) if n else empty, n_cells, sp, slack_abs=slack[k], slack_rel=0.0)
+            dev[k] = sp
+        return dev
+
+    stream = torch.cuda.current_stream()
+    res = {"workload": "au_foil_16384cells_poisson256_Z79_Zstar10-40_brems_bh_dt1fs", "cells": n_cells,
+           "materials": len(wl.materials)}
+    dev = state()
+    ctx.read_status()
+    ctx.steps_capture(n_cells, mat, wl.ion_mass, dev["em"], dev["ep"], dev["ph"], dev["ion"], wl.dt, wl.seed,
+                      step0=0, n_steps=steps, mask=mask, precision=pcc.FP32_BATCHED)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ctx.steps_launch()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    status, st = ctx.read_status()
+    res["fp32_batched"] = {"steps": steps, "ms_per_step": ms / steps, "value": sum(st["pairs"]) / (ms * 1e-3),
+                           "events": sum(st["created"]), "unit": UNIT, "status": status,
+                           "timed": f"{steps} steps in one CUDA graph"}
+    dev = state()
+    times, pairs = [], 0
+    for s in range(plain_steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pcc.collide(ctx, n_cells, mat, wl.ion_mass, dev["em"], dev["ep"], dev["ph"], dev["ion"], wl.dt, wl.seed, s,
+                    mask=mask, precision=pcc.FP64_PLAIN)
+        for k in ("em", "ep", "ph"):
+            pcc.append_secondaries(ctx, n_cells, dev[k])
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    status, st = ctx.read_status()
+    m = float(np.mean(times))
+    res["fp64_plain"] = {"steps": plain_steps, "ms_per_step": m, "value": sum(st["pairs"]) / plain_steps / (m * 1e-3),
+                         "unit": UNIT, "status": status, "timed": "eager steps, CUDA events"}
+    res["speedup_of_batched"] = m / res["fp32_batched"]["ms_per_step"]
     return res
 
 
@@ -463,41 +580,78 @@ def e2e_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, 
 
 
 # ---------------------------------------------------------- CPU oracle leg --
-def oracle_sample(counts, budget_s, seed=11):
-    """Run the FP64 oracle on a random 1/256 subset of the cells for about
-    budget_s seconds of CPU time; returns pairs/s and the sample description."""
-    from oracle import oracle as orc
-    from paper_1907_02814_gb300 import workloads as W
-    n_cells = len(counts["e"])
-    rng = np.random.default_rng(seed)
-    sub = np.sort(rng.choice(n_cells, n_cells // 256, replace=False))
-    data = W.batched_cu_host(counts, cells=sub)
-    remap = np.zeros(n_cells, np.int32)
-    remap[sub] = np.arange(len(sub), dtype=np.int32)
-    for d in data.values():
-        if len(d["cell"]):
-            d["cell"] = remap[d["cell"]]
-    m = counts["material"]
-    T = orc.OracleTables([orc.material(m.Z, m.Zstar, m.n_i, m.T_e)], orc.table_spec())
-    sp = {k: orc.OracleSpecies(v, cap=len(v["w"]) + 200000) for k, v in data.items()}
-    mats = np.zeros(len(sub), np.int32)
-    pairs = 0.0
-    steps = 0
-    t0 = time.process_time()
-    while True:
-        _, st = orc.step(T, len(sub), mats, sp["em"], sp["ep"], sp["ph"], sp["ion"], counts["ion_mass"],
-                         counts["dt"], counts["seed"], steps)
-        pairs += sum(st["pairs"])
-        steps += 1
-        if time.process_time() - t0 >= budget_s:
-            break
-    el = time.process_time() - t0
-    return pairs / el, f"{len(sub)} of {n_cells} cells (1/256, same occupancy law), {steps} oracle steps", steps
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OracleSample:
+    """The FP64 oracle on a fixed random 1/256 subset of the cells (same
+    occupancy law), stepped in place; threads = OpenMP threads over cells."""
+
+    def __init__(self, counts, seed=11):
+        from oracle import oracle as orc
+        from paper_1907_02814_gb300 import workloads as W
+        self.orc = orc
+        self.counts = counts
+        n_cells = len(counts["e"])
+        rng = np.random.default_rng(seed)
+        self.sub = np.sort(rng.choice(n_cells, n_cells // 256, replace=False))
+        self.data = W.batched_cu_host(counts, cells=self.sub)
+        remap = np.zeros(n_cells, np.int32)
+        remap[self.sub] = np.arange(len(self.sub), dtype=np.int32)
+        for d in self.data.values():
+            if len(d["cell"]):
+                d["cell"] = remap[d["cell"]]
+        m = counts["material"]
+        self.T = orc.OracleTables([orc.material(m.Z, m.Zstar, m.n_i, m.T_e)], orc.table_spec())
+        self.mats = np.zeros(len(self.sub), np.int32)
+        self.reset()
+        self.describe = f"{len(self.sub)} of {n_cells} cells (1/256, same occupancy law, fixed subset)"
+
+    def reset(self):
+        self.sp = {k: self.orc.OracleSpecies(v, cap=len(v["w"]) + 200000) for k, v in self.data.items()}
+        self.steps = 0
+
+    def step(self, threads):
+        """One oracle step; returns (pairs, wall seconds)."""
+        self.orc.set_threads(threads)
+        c = self.counts
+        t0 = time.perf_counter()
+        _, st = self.orc.step(self.T, len(self.sub), self.mats, self.sp["em"], self.sp["ep"], self.sp["ph"],
+                              self.sp["ion"], c["ion_mass"], c["dt"], c["seed"], self.steps)
+        el = time.perf_counter() - t0
+        self.orc.set_threads(1)
+        self.steps += 1
+        return sum(st["pairs"]), el
+
+    def rate(self, threads, budget_s):
+        """pairs/s over whole steps from the initial state, for about budget_s
+        seconds of wall time."""
+        self.reset()
+        pairs = el = 0.0
+        while True:
+            p, t = self.step(threads)
+            pairs += p
+            el += t
+            if el >= budget_s:
+                return pairs / el, self.steps
 
 
 def cpu_baseline(counts, budget_s=10.0):
-    v, sample, _ = oracle_sample(counts, budget_s)
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    """The oracle timed on this host's cores: single-threaded and with OpenMP
+    threads over the cells on every core this process may use."""
+    cores = host_cores()
+    s = OracleSample(counts)
+    v1, n1 = s.rate(1, 0.5 * budget_s)
+    threads = s.orc.set_threads(cores)
+    s.orc.set_threads(1)
+    vm, nm = s.rate(threads, 0.5 * budget_s)
+    return {"value": vm, "unit": UNIT, "cores": threads, "cores_available": cores, "value_1t": v1,
+            "value_omp": vm, "threads_omp": threads, "kind": "oracle",
+            "sample": f"{s.describe}; {n1} steps single-threaded, {nm} steps on {threads} threads"}
 
 
 def run_reference(args):
@@ -506,17 +660,26 @@ def run_reference(args):
         return
     from paper_1907_02814_gb300 import workloads as W
     counts = workload_counts(W, args.cells, 3)
-    per_step = []
-    for s in range(args.warmup + args.steps):
-        v, sample, _ = oracle_sample(counts, budget_s=args.cpu_budget / max(1, args.steps + args.warmup), seed=11 + s)
-        if s >= args.warmup:
-            per_step.append(v)
-    value = float(np.mean(per_step))
+    s = OracleSample(counts)
+    cores = host_cores()
+    threads = s.orc.set_threads(cores)
+    s.orc.set_threads(1)
+    for _ in range(args.warmup):
+        s.step(threads)
+    pairs = el = 0.0
+    for _ in range(args.steps):
+        p, t = s.step(threads)
+        pairs += p
+        el += t
+    value = pairs / el
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(args.cells), "precision": "fp64 oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.cells), "precision": "fp64 oracle",
+                   "sample": s.describe + " stepped in place; one oracle step per bench step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "cores_available": cores, "kind": "oracle",
+                         "sample": f"{s.describe}; {args.steps} timed steps after {args.warmup} on {threads} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -534,6 +697,7 @@ def main():
     ap.add_argument("--cells", type=int, default=FULL_CELLS, help="smaller cases keep the occupancy law")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 path (0: skip)")
     ap.add_argument("--no-emission", action="store_true")
+    ap.add_argument("--no-config2", action="store_true", help="skip the Au foil (16384-cell) leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

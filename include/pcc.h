@@ -46,6 +46,10 @@ typedef enum {
 #define PCC_ST_ID_RANGE    0x10u  /* cell >= 2^24, step >= 2^19 or > 65536 pairs per cell:
                                      secondary identifiers are no longer unique          */
 #define PCC_ST_TIMEOUT     0x20u  /* a bounded wait (bulk copy barrier) gave up          */
+#define PCC_ST_BOUND_RANGE 0x40u  /* batched path only: an evaluated pair had an ion-frame
+                                     Lorentz factor above 1e7, where the Trident bound of
+                                     the quick reject is no longer proven, so pairs of that
+                                     energy may have been rejected without evaluation     */
 
 typedef enum { PCC_FP64_PLAIN = 0, PCC_FP32_BATCHED = 1 } pcc_precision;
 
@@ -273,16 +277,22 @@ int pcc_totals(pcc_ctx *ctx, int n_cells, const pcc_species *sp, int is_photon, 
 
 /* Allocation-free variant of pcc_totals (no counterpart in the paper; a
  * service for callers that may not allocate device memory while they run,
- * such as a simulation that sizes all its buffers at start-up, an
- * application whose own allocator owns the device, or a step being recorded
- * into a CUDA graph).  Same result as pcc_totals up to the order of the FP64
+ * such as a simulation that sizes all its buffers at start-up and forbids
+ * allocation in its time loop, or an application whose own allocator owns
+ * the whole device).  Same result as pcc_totals up to the order of the FP64
  * sums; needs no context.  Its scratch is a fixed 96 KiB array in the
  * library's device memory (held by every GPU that loads the library until
  * the process exits), so n_cells is limited to 4,194,304: larger counts
- * return PCC_E_CAPACITY without launching anything.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  Calls share the array: two
- * calls whose kernels can run at the same time (unordered streams) race.
+ * return PCC_E_CAPACITY without launching anything.  The first call in a
+ * CUDA context (normally once per device, with that device current) looks
+ * up the array's device address with cudaGetSymbolAddress and caches it per
+ * context; make that first call before any stream capture.  A context
+ * created anew (after cudaDeviceReset, or a second context on the device)
+ * gets its own lookup on its first call.  Calls share the array and it
+ * keeps the last call's partial sums (each call overwrites the entries it
+ * reads, so nothing needs clearing); two calls whose kernels can run at the
+ * same time (unordered streams) race.  Allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
  * out: device double[3].  Asynchronous after the first call. */
 int pcc_totals_noalloc(int n_cells, const pcc_species *sp, int is_photon, double *out, void *stream);
 

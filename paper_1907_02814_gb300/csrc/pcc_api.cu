@@ -67,6 +67,7 @@ extern "C" const char* pcc_status_bit_string(unsigned bit)
     case PCC_ST_NONFINITE: return "PCC_ST_NONFINITE";
     case PCC_ST_ID_RANGE: return "PCC_ST_ID_RANGE";
     case PCC_ST_TIMEOUT: return "PCC_ST_TIMEOUT";
+    case PCC_ST_BOUND_RANGE: return "PCC_ST_BOUND_RANGE";
     default: return "unknown status bit";
     }
 }

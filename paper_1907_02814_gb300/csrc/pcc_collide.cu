@@ -435,6 +435,8 @@ __device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb,
     const Real uu[3] = {(Real)u[0], (Real)u[1], (Real)u[2]};
     to_ion_frame(f, uu);
     if (!isfinite(f.gl)) { acc.status |= PCC_ST_NONFINITE; return; }
+    // the batched path's Trident quick-reject bound is proven up to gamma' = 1e7
+    if (sizeof(Real) == 4 && (a.mask & PCC_TRIDENT) && f.Tp > (Real)(1e7 - 1.0)) acc.status |= PCC_ST_BOUND_RANGE;
     if (a.mask & PCC_BREMS) {
         const Real sig = sigma_at<Real>(tb, tb.bsig + (size_t)mat * a.g.n_rows, a.g, f.Tp, acc.status);
         const Real x = q_div(coef * sig * f.pp, f.gl * f.gi);

@@ -248,10 +248,19 @@ __device__ CellScreen cell_screen(const float* p, int Z)
     if (!c.ok) return c;
     c.LTF = c.sTF * exp(-log((double)Z) / 3.0) / kAlpha;
     const double ri = cbrt(3.0 / (4.0 * kPi * c.n_i));
-    double lam = 0.0;
-    if (c.Zs > 0.0) lam = sqrt(kEps0 * c.T_e / (kQe * c.n_i * c.Zs * (c.Zs + 1.0)));
-    c.debye = lam > ri;
-    c.LD = c.sD * fmax(lam, ri) / kRc;
+    if (c.Zs > 0.0) {
+        const double lam = sqrt(kEps0 * c.T_e / (kQe * c.n_i * c.Zs * (c.Zs + 1.0)));
+        c.debye = lam > ri;
+        c.LD = c.sD * fmax(lam, ri) / kRc;
+    } else {
+        // Z* = 0: Eq. LDH gives lambda_D = infinity.  Nothing depends on L_D
+        // then (eta_D = 0), and the derivative with respect to Z* is the limit
+        // from Z* > 0, in which the cross terms take their L_D -> infinity
+        // values.  A finite stand-in 1e5 L_TF gives those limits to ~1e-9
+        // and keeps every FP32 product of the non-relativistic duals finite.
+        c.debye = false;
+        c.LD = 1e5 * c.LTF;
+    }
     c.etaD = c.Zs / Z;
     c.etaTF = 1.0 - c.etaD;
     c.a = i_tfd(c.etaTF, c.LTF, c.etaD, c.LD);
@@ -539,14 +548,16 @@ __global__ void __launch_bounds__(kEmThreads, GRAD ? 2 : 4) emission_kernel(cons
     const double teD = deD + dLR * dLR_da * da_deD;
     // d(L_TF, L_D, eta_D)/d theta
     double dLD_dth[5] = {0, 0, 0, 0, 0};
-    if (cs.debye) {
+    if (cs.Zs == 0.0) {
+        // no path through L_D (see cell_screen)
+    } else if (cs.debye) {
         dLD_dth[0] = -0.5 * cs.LD / cs.n_i;
         dLD_dth[1] = 0.5 * cs.LD / cs.T_e;
         dLD_dth[2] = -0.5 * cs.LD * (2.0 * cs.Zs + 1.0) / (cs.Zs * (cs.Zs + 1.0));
     } else {
         dLD_dth[0] = -cs.LD / (3.0 * cs.n_i);
     }
-    dLD_dth[4] = cs.LD / cs.sD;
+    if (cs.Zs != 0.0) dLD_dth[4] = cs.LD / cs.sD;
     const double dLTF_dsTF = cs.LTF / cs.sTF;
     const double deD_dZs = 1.0 / a.Z;
     const double scale = cs.n_i * C0;

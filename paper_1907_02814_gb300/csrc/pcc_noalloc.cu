@@ -2,18 +2,23 @@
 //
 // Some callers cannot allocate device memory while they run: a simulation
 // code that sizes every device buffer once at start-up and forbids
-// allocation inside its time loop, a host application whose own allocator
-// owns the whole device, or a step being recorded into a CUDA graph, where a
-// cudaMalloc would break the capture.  pcc_totals obtains its scratch (the
+// allocation inside its time loop, or a host application whose own
+// allocator owns the whole device and would see a library allocation as a
+// leak or a fragmentation hazard.  pcc_totals obtains its scratch (the
 // per-block partial sums) from the context, which may allocate; this variant
 // uses a fixed array in the library's own device memory instead.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds its 96 KiB until the process exits.  Host code cannot use
-// its name as a device address, so the address is looked up once per device
-// with cudaGetSymbolAddress (on the first call on that device) and passed to
-// the kernels.  All calls share the array: calls whose kernels overlap on the
-// GPU (different streams without ordering) race on it.
+// its name as a device address, so the address is looked up with
+// cudaGetSymbolAddress, with the device current, on the first call in each
+// CUDA context, and passed to the kernels.  The lookup is cached per context
+// (keyed by the driver's context identifier, which is never reused), so a
+// context created anew after cudaDeviceReset, or a second context on the
+// same device, gets its own address instead of a stale one.  All calls
+// share the array: calls whose kernels overlap on the GPU (different
+// streams without ordering) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -26,7 +31,6 @@ namespace {
 constexpr int kCellsPerBlock = 1024;
 constexpr int kMaxBlocks = 4096;                       // at most 4,194,304 cells
 constexpr long long kMaxCells = (long long)kCellsPerBlock * kMaxBlocks;
-constexpr int kMaxDevices = 64;
 
 // Per-block partial sums {sum W, sum W E, sum W |u|}; every block of a call
 // writes its own three entries before the reduction reads them, so nothing
@@ -34,7 +38,12 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_partial[3 * kMaxBlocks];
 
 std::mutex g_mutex;
-double* g_partial_ptr[kMaxDevices] = {};
+
+// Scratch addresses already looked up, by CUDA context identifier.
+struct CachedAddress { unsigned long long ctx_id; double* ptr; };
+constexpr int kMaxContexts = 64;
+CachedAddress g_cache[kMaxContexts] = {};
+int g_cache_next = 0;
 
 // Block b sums the live particles of cells [b * 1024, (b + 1) * 1024), one warp
 // per cell at a time, lanes over particles; fixed-order reduction.
@@ -79,24 +88,68 @@ __global__ void totals_sum_kernel(const double* __restrict__ partial, int nb, do
     out[2] = t2;
 }
 
-// Device address of g_partial on the current device, looked up once per device.
+// Identifier of the CUDA context current on this thread (cuCtxGetId; unique
+// within the process and never reused).  The two driver calls are resolved
+// through the runtime, so the library does not link the driver library.
+// *id = 0 when no context is current yet.
+int current_context_id(unsigned long long* id)
+{
+    using GetCurrentFn = CUresult (*)(CUcontext*);
+    using GetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    *id = 0;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return pcc::cuda_fail(e, "pcc_totals_noalloc: cudaGetDriverEntryPointByVersion");
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            pcc::set_error("pcc_totals_noalloc: the driver does not provide cuCtxGetCurrent/cuCtxGetId");
+            return PCC_E_CUDA;
+        }
+        get_current = reinterpret_cast<GetCurrentFn>(f1);
+        get_id = reinterpret_cast<GetIdFn>(f2);
+    }
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS) {
+        pcc::set_error("pcc_totals_noalloc: cuCtxGetCurrent failed");
+        return PCC_E_CUDA;
+    }
+    if (c && get_id(c, id) != CUDA_SUCCESS) {
+        pcc::set_error("pcc_totals_noalloc: cuCtxGetId failed");
+        return PCC_E_CUDA;
+    }
+    return PCC_OK;
+}
+
+// Device address of g_partial in the current context: looked up with
+// cudaGetSymbolAddress on the first call in each context, then cached.
 int partial_address(double** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return pcc::cuda_fail(e, "pcc_totals_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) {
-        pcc::set_error("pcc_totals_noalloc: device index " + std::to_string(dev) + " out of range");
-        return PCC_E_INVALID;
-    }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_partial_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_partial);
-        if (e != cudaSuccess) return pcc::cuda_fail(e, "pcc_totals_noalloc: cudaGetSymbolAddress");
-        g_partial_ptr[dev] = static_cast<double*>(p);
+    unsigned long long id = 0;
+    int rc = current_context_id(&id);
+    if (rc != PCC_OK) return rc;
+    if (id != 0) {
+        for (const CachedAddress& c : g_cache)
+            if (c.ctx_id == id) { *out = c.ptr; return PCC_OK; }
     }
-    *out = g_partial_ptr[dev];
+    // first call in this context (cudaGetSymbolAddress also creates the
+    // device's primary context when none is current yet)
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_partial);
+    if (e != cudaSuccess) return pcc::cuda_fail(e, "pcc_totals_noalloc: cudaGetSymbolAddress");
+    rc = current_context_id(&id);
+    if (rc != PCC_OK) return rc;
+    if (id != 0) {
+        g_cache[g_cache_next] = {id, static_cast<double*>(p)};
+        g_cache_next = (g_cache_next + 1) % kMaxContexts;
+    }
+    *out = static_cast<double*>(p);
     return PCC_OK;
 }
 

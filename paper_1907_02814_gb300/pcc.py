@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libpcc.so")
 
 PCC_OK, PCC_E_INVALID, PCC_E_CUDA, PCC_E_CAPACITY, PCC_E_NO_TABLES = 0, 1, 2, 3, 4
 ST_TABLE_RANGE, ST_PROB_LARGE, ST_CAPACITY, ST_NONFINITE, ST_ID_RANGE, ST_TIMEOUT = 1, 2, 4, 8, 16, 32
+ST_BOUND_RANGE = 64
 FP64_PLAIN, FP32_BATCHED = 0, 1
 BREMS, TRIDENT, BH = 1, 2, 4
 GROUP_EM, GROUP_EP, GROUP_PH = 0x100, 0x200, 0x400

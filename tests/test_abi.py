@@ -66,12 +66,13 @@ def test_status_strings_without_a_device(lib):
     assert L.pcc_status_string(-1) == b"unknown return code"
     bits = {pcc.ST_TABLE_RANGE: "PCC_ST_TABLE_RANGE", pcc.ST_PROB_LARGE: "PCC_ST_PROB_LARGE",
             pcc.ST_CAPACITY: "PCC_ST_CAPACITY", pcc.ST_NONFINITE: "PCC_ST_NONFINITE",
-            pcc.ST_ID_RANGE: "PCC_ST_ID_RANGE", pcc.ST_TIMEOUT: "PCC_ST_TIMEOUT"}
+            pcc.ST_ID_RANGE: "PCC_ST_ID_RANGE", pcc.ST_TIMEOUT: "PCC_ST_TIMEOUT",
+            pcc.ST_BOUND_RANGE: "PCC_ST_BOUND_RANGE"}
     for bit, name in bits.items():
         assert L.pcc_status_bit_string(bit).decode() == name
     assert L.pcc_status_bit_string(0) == b"unknown status bit"
     assert L.pcc_status_bit_string(3) == b"unknown status bit"
-    assert L.pcc_status_bit_string(0x40) == b"unknown status bit"
+    assert L.pcc_status_bit_string(0x80) == b"unknown status bit"
     assert pcc.status_bits(pcc.ST_TIMEOUT | pcc.ST_TABLE_RANGE) == ["PCC_ST_TABLE_RANGE", "PCC_ST_TIMEOUT"]
     with pytest.raises(pcc.PccError, match="PCC_E_INVALID"):
         pcc._check(L.pcc_create(None, 0), "pcc_create")

@@ -60,3 +60,33 @@ def test_peaks_prefer_the_measured_file(tmp_path, monkeypatch):
     assert bench.peaks() == (bench.FALLBACK_HBM, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6657.6}))
     assert bench.peaks() == (6657.6, "measured")
+
+
+def test_emission_instruction_counts_follow_the_kernel_sources(tmp_path, monkeypatch):
+    root = tmp_path / "root"
+    csrc = root / "paper_1907_02814_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in bench.EMISSION_SOURCES:
+        shutil.copy(os.path.join(bench.ROOT, "paper_1907_02814_gb300", "csrc", f), csrc / f)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    h = bench.emission_source_hash()
+    (root / "profiles").mkdir()
+    (root / "profiles" / bench.EMISSION_PROFILE).write_text(
+        f"# x\nsource_hash: {h}\n\n## void emission_kernel<0>  (forward)\n- warp instructions: 1000.0 inst\n"
+        "## void emission_kernel<1>  (adjoint)\n- duration: 1 ms\n- warp instructions: 2500.5 inst\n")
+    assert bench.emission_instructions() == {"fwd": 1000.0, "bwd": 2500.5}
+    with open(csrc / bench.EMISSION_SOURCES[0], "a") as f:
+        f.write("\n// changed\n")
+    assert bench.emission_instructions() is None
+
+
+def test_cpu_baseline_states_its_cores(monkeypatch):
+    """Both oracle legs on a small case of the bench workload: single-threaded
+    and on every core this process may use, with the core count stated."""
+    from paper_1907_02814_gb300 import workloads as W
+    counts = bench.workload_counts(W, 1 << 14, 3)
+    out = bench.cpu_baseline(counts, budget_s=0.2)
+    assert out["cores_available"] == bench.host_cores() >= 1
+    assert out["value_1t"] > 0 and out["value_omp"] > 0 and out["value"] == out["value_omp"]
+    assert 1 <= out["cores"] <= out["cores_available"] and out["kind"] == "oracle"
+    assert "fixed subset" in out["sample"]

@@ -89,6 +89,51 @@ def test_gradient_matches_oracle(pcc, ctx, orc, data):
         assert np.all(err <= 1e-3 * abs(f) + 1e-3 * np.abs(th * ref)), (i, gp[i], ref, f)
 
 
+def test_gradient_matches_analytic_oracle(pcc, ctx, orc, data):
+    """Adjoint kernel vs the oracle's analytic FP64 gradient (the chain rule
+    written out by hand, independent of any differencing), per component:
+    |theta_k (g_k - ref_k)| <= 1e-4 (|f| + |theta_k ref_k|).  Cells: the
+    workload's own on both branches of max(lambda_D, r_i), plus Z* = 0 (the
+    Z* derivative is the limit from Z* > 0 on both sides) and Z* = Z, with
+    samples across the non-relativistic, relativistic and ultra-relativistic
+    regimes."""
+    rng = np.random.default_rng(7)
+    Z = data["Z"]
+    deb, ri = [], []
+    for c in rng.permutation(len(data["params"])):
+        if not away_from_kink(orc, Z, data["params"][c]):
+            continue
+        s = orc.screening(oracle_material(orc, Z, data["params"][c]))
+        (deb if s.lambdaD > s.ri else ri).append(c)
+        if len(deb) >= 6 and len(ri) >= 6:
+            break
+    cells = deb[:6] + ri[:6]
+    p = data["params"][cells].copy()
+    g = data["gamma"][cells].copy()
+    w = data["w"][cells].copy()
+    extra = np.array([[8.5e28, 100.0, 0.0, 1.0, 1.0], [1e25, 5e3, 0.0, 1.0, 1.0],
+                      [3e27, 2e3, float(Z), 1.0, 1.0], [1e26, 1e4, float(Z), 1.1, 0.9]], np.float32)
+    T = (10.0 ** rng.uniform(np.log10(0.05), np.log10(200.0), (4, g.shape[1])) / 0.51099895).astype(np.float32)
+    p = np.concatenate([p, extra])
+    g = np.concatenate([g, 1.0 + T])
+    w = np.concatenate([w, rng.uniform(0.5, 2.0, (4, g.shape[1])).astype(np.float32)])
+    gout = rng.uniform(0.5, 1.5, (len(p), 3)).astype(np.float32)
+    gp = pcc.expected_emission_bwd(ctx, Z, to_dev(p), to_dev(g), to_dev(w), to_dev(gout)).cpu().numpy()
+    st, _ = ctx.read_status()
+    assert st == 0
+    worst = 0.0
+    for i in range(len(p)):
+        mat = oracle_material(orc, Z, p[i])
+        gg, ww = g[i].astype(np.float64), w[i].astype(np.float64)
+        ref = orc.expected_emission_grad_analytic(mat, gg, ww, gout[i].astype(np.float64))
+        f = float(np.dot(gout[i], orc.expected_emission(mat, gg, ww)))
+        th = p[i].astype(np.float64)
+        err = np.abs(th * (gp[i] - ref)) / (abs(f) + np.abs(th * ref))
+        worst = max(worst, float(err.max()))
+        assert np.all(err <= 1e-4), (i, p[i], gp[i], ref, err)
+    print(f"\n[emission] adjoint vs analytic FP64 gradient: worst scaled error {worst:.1e} over {len(p)} cells")
+
+
 def test_gradient_matches_fd_of_fp32_forward(pcc, ctx, orc, data):
     """Adjoint vs central differences (h = 1e-3 relative) of the GPU forward
     itself; the FP32 forward's ~1e-6 noise over 2h bounds the comparison

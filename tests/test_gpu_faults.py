@@ -112,6 +112,43 @@ def test_nonfinite_momentum_is_flagged(pcc, ctx, precision):
     assert stats[0]["pairs"][0] == 8 * 32
 
 
+def test_batched_flags_only_conditions_met_by_evaluated_pairs(pcc, ctx):
+    """The documented difference between the paths: the batched FP32 path
+    reads a projectile's momentum only for pairs that pass the quick reject,
+    so a NaN momentum and an energy above the table in cells whose pairs are
+    all rejected from their accept words alone raise no status bit there,
+    while the plain FP64 path, which evaluates every pair, flags both.  With
+    dt = 1e-22 s the per-material bound gives an accept threshold of 0, so
+    no pair is a candidate; no event happens on either path."""
+    wl = W.solid_cu(n_cells=8, e_per_cell=32, i_per_cell=8, seed=48, dt=1e-22, T_mev=2.0)
+    em = {k: (v.copy() if v is not None else None) for k, v in wl.species["em"].items()}
+    em["ux"][3] = np.nan
+    g = 5000.0                        # above the table's gamma_max = 2000
+    em["ux"][17], em["uy"][17], em["uz"][17] = np.sqrt(g * g - 1.0), 0.0, 0.0
+    species = dict(wl.species, em=em)
+    _, st64, stats64 = run(pcc, ctx, wl, "fp64", species=species)
+    _, st32, stats32 = run(pcc, ctx, wl, "fp32", species=species)
+    assert st64 & pcc.ST_NONFINITE and st64 & pcc.ST_TABLE_RANGE
+    assert stats32[0]["candidates"][0] == 0
+    assert st32 == 0, pcc.status_bits(st32)
+    assert stats64[0]["pairs"] == stats32[0]["pairs"] and stats64[0]["pairs"][0] == 8 * 32
+    assert sum(stats64[0]["created"]) == sum(stats32[0]["created"]) == 0
+
+
+@pytest.mark.parametrize("gamma,flagged", [(2e7, True), (1e6, False)])
+def test_trident_bound_range_is_flagged(pcc, ctx, gamma, flagged):
+    """The batched path's Trident quick-reject bound is proven for ion-frame
+    Lorentz factors up to 1e7: an evaluated pair above it raises
+    PCC_ST_BOUND_RANGE (batched path only; the plain path has no bound).  The
+    step is long enough that every pair is a candidate."""
+    wl = W.solid_cu(n_cells=4, e_per_cell=16, i_per_cell=4, seed=49, dt=1e-10, beam_gamma=gamma)
+    _, st32, stats32 = run(pcc, ctx, wl, "fp32", mask=pcc.TRIDENT)
+    _, st64, _ = run(pcc, ctx, wl, "fp64", mask=pcc.TRIDENT)
+    assert stats32[0]["candidates"][0] == 4 * 16
+    assert bool(st32 & pcc.ST_BOUND_RANGE) == flagged, pcc.status_bits(st32)
+    assert st64 & pcc.ST_BOUND_RANGE == 0
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_material_index_out_of_range_is_flagged(pcc, ctx, precision):
     """A cell whose material index is past the tables: PCC_ST_NONFINITE, and

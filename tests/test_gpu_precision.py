@@ -1,17 +1,36 @@
-"""Precision study (FP32 batched path vs FP64 GPU path vs FP64 oracle) on
-Ta and Al targets over Z* in {0, Z/4, Z/2, 3Z/4, Z} and T_e in {10, 1e2,
-1e3, 1e4} eV, with the c2 (foil) electron and photon populations and ions at
-rest.  Reports and bounds, per result:
-  - cross-section tables: relative error of the FP32 ln-sigma copies;
-  - events: the FP64 GPU path reproduces the oracle exactly; the FP32 path
-    differs in a fraction of pairs below 1e-5;
-  - ledgers: radiated energy per cell, FP32 Kahan ledger vs FP64 oracle;
-  - spectra: first two moments of the created photon energies;
-  - conservation: per-step drift of total energy (rest mass included) and
-    charge, from the FP64 global reductions (pcc_totals).
-Run with -s to see the table."""
+"""Precision study, per material state: the FP32 batched path and the FP64
+GPU path against the FP64 oracle on Ta (Z = 73) and Al (Z = 13) targets,
+Z* in {0, Z/4, Z/2, 3Z/4, Z} and T_e in {10, 1e2, 1e3, 1e4} eV (40 states),
+with the foil-shaped electron and photon populations and ions at rest.
+
+Each step starts both GPU paths from the oracle's own state before that
+step (binned onto the device), so every accept decision is compared on
+identical inputs and a differing decision cannot spread into later steps.
+Per state and per path the study records and bounds:
+  - table: relative error of sigma from the FP32 ln-sigma copies the
+    batched kernels read, against the oracle's FP64 sigma (Brems and BH);
+  - decisions: distinct events (one per secondary identifier without its
+    last bit) present on one side only, per pair;
+  - sampling: for the photons of events both sides made, the relative
+    energy difference; above 1e-4 it is counted as a sampling decision (the
+    stochastic row pick or the CDF column) taken the other way near its
+    threshold, and the largest difference of the rest is the rounding error;
+  - ledgers: per-cell radiated energy and created weight (Kahan FP32 on the
+    GPU, FP64 in the oracle), over cells whose events and sampling decisions
+    agree;
+  - spectra: mean and mean square of the created photon energies over the
+    events both sides made, and a two-sample Kolmogorov-Smirnov test over
+    all created photons;
+  - conservation: per-step relative change of the total energy (rest mass
+    included) and of the charge of the leptons and photons.
+Set PCC_PRECISION_TABLE to a file path to write the per-state table as
+markdown; run with -s to see it."""
+import os
+
 import numpy as np
 import pytest
+
+import precision_study as PS
 
 torch = pytest.importorskip("torch")
 
@@ -21,6 +40,9 @@ from paper_1907_02814_gb300 import workloads as W  # noqa: E402
 
 TABLE = dict(n_rows=128, n_cols=128)
 STEPS = 3
+CELLS_PER_STATE = 2048
+DT = 100e-15
+LEPTONS = ("em", "ep", "ph")
 
 
 @pytest.fixture(scope="module")
@@ -34,140 +56,228 @@ def pcc():
 
 @pytest.fixture(scope="module")
 def study(pcc, orc):
+    wl = W.precision_study(cells_per_material=CELLS_PER_STATE, dt=DT)
+    n_cells, n_states = wl.n_cells, len(wl.materials)
+    state = np.asarray(wl.material_of_cell, dtype=np.int64)
     ctx = pcc.Context(0)
-    wl = W.precision_study(cells_per_material=24, dt=100e-15)
-    mats = [pcc.material(m.Z, m.Zstar, m.n_i, m.T_e) for m in wl.materials]
-    ctx.tables_build(mats, pcc.table_spec(**TABLE))
+    ctx.tables_build([pcc.material(m.Z, m.Zstar, m.n_i, m.T_e) for m in wl.materials], pcc.table_spec(**TABLE))
     gt = ctx.tables_read()
-    mat = torch.as_tensor(wl.material_of_cell, device="cuda")
-
-    def to_device():
-        dev = {}
-        for name, d in wl.species.items():
-            n = len(d["w"])
-            sp = pcc.DeviceSpecies.empty(wl.n_cells, n + 4096 * wl.n_cells + n)
-            pcc.bin(ctx, pcc.particles_to_device(d), wl.n_cells, sp, slack_abs=4096, slack_rel=1.0)
-            dev[name] = sp
-        return dev
-
-    def energy_charge(dev):
-        e = sum(float(pcc.totals(ctx, wl.n_cells, dev[k], is_photon=(k == "ph"))[1]) for k in ("em", "ep", "ph"))
-        q = float(pcc.totals(ctx, wl.n_cells, dev["ep"])[0]) - float(pcc.totals(ctx, wl.n_cells, dev["em"])[0])
-        return e, q
-
-    runs = {}
-    for label, prec in (("fp64", pcc.FP64_PLAIN), ("fp32", pcc.FP32_BATCHED)):
-        dev = to_device()
-        ledger = torch.zeros((wl.n_cells, 4), dtype=torch.float32, device="cuda")
-        ctx.read_status()
-        eq = [energy_charge(dev)]
-        per_step = []
-        for s in range(STEPS):
-            pcc.collide(ctx, wl.n_cells, mat, wl.ion_mass, dev["em"], dev["ep"], dev["ph"], dev["ion"], wl.dt,
-                        wl.seed, s, precision=prec, ledger=ledger)
-            for k in ("em", "ep", "ph"):
-                pcc.append_secondaries(ctx, wl.n_cells, dev[k])
-            eq.append(energy_charge(dev))
-            per_step.append(ctx.read_status())
-            if s == 0:
-                first = {k: dev[k].live_host() for k in ("em", "ep", "ph")}
-        led = ledger.cpu().numpy().astype(np.float64)
-        runs[label] = {"eq": eq, "status": [p[0] for p in per_step], "stats": [p[1] for p in per_step],
-                       "first": first, "final": {k: dev[k].live_host() for k in ("em", "ep", "ph")},
-                       "ledger": np.stack([led[:, 0] - led[:, 1], led[:, 2] - led[:, 3]], 1)}
-
     T = orc.OracleTables([orc.material(m.Z, m.Zstar, m.n_i, m.T_e) for m in wl.materials], orc.table_spec(**TABLE))
-    sp = {k: orc.OracleSpecies(v, cap=len(v["w"]) + 200000) for k, v in wl.species.items()}
-    oled = np.zeros((wl.n_cells, 2))
-    ost = []
+    mat = torch.as_tensor(wl.material_of_cell, device="cuda")
+    ion = pcc.DeviceSpecies.empty(n_cells, len(wl.species["ion"]["w"]) + n_cells)
+    pcc.bin(ctx, pcc.particles_to_device(wl.species["ion"]), n_cells, ion, slack_abs=1, slack_rel=0.0)
+
+    sp = {k: orc.OracleSpecies(v, cap=len(v["w"]) + 4_000_000) for k, v in wl.species.items()}
+    labels = ("fp64", "fp32")
+    rec = {lab: {"mism": np.zeros(n_states), "flips": np.zeros(n_states), "kerr": np.zeros(n_states),
+                 "led_err": np.zeros((n_states, 2)), "m1": np.zeros(n_states),
+                 "m2": np.zeros(n_states), "de": np.zeros((STEPS, n_states)), "dq": np.zeros((STEPS, n_states)),
+                 "k": [[] for _ in range(n_states)], "k_match": [[] for _ in range(n_states)],
+                 "status": [], "pairs_total": [], "kerr_all": []} for lab in labels + ("oracle",)}
+    pairs = np.zeros(n_states)
+    events = np.zeros(n_states)
+    k_orc = [[] for _ in range(n_states)]
+    k_orc_match = {lab: [[] for _ in range(n_states)] for lab in labels}
+
+    def energy_charge(d):
+        e = sum(PS.energy_per_cell(d[k], n_cells, k == "ph") for k in LEPTONS)
+        q = PS.weight_per_cell(d["ep"], n_cells) - PS.weight_per_cell(d["em"], n_cells)
+        qa = PS.weight_per_cell(d["ep"], n_cells) + PS.weight_per_cell(d["em"], n_cells)
+        return PS.by_state(e, state, n_states), PS.by_state(q, state, n_states), PS.by_state(qa, state, n_states)
+
     for s in range(STEPS):
-        _, st = orc.step(T, wl.n_cells, wl.material_of_cell, sp["em"], sp["ep"], sp["ph"], sp["ion"], wl.ion_mass,
-                         wl.dt, wl.seed, s, ledger=oled)
-        ost.append(st)
-        if s == 0:
-            ofirst = {k: sp[k].canonical() for k in ("em", "ep", "ph")}
-    orc_run = {"stats": ost, "first": ofirst, "final": {k: sp[k].canonical() for k in ("em", "ep", "ph")},
-               "ledger": oled}
-    yield {"wl": wl, "gpu_tables": gt, "orc_tables": T, "runs": runs, "orc": orc_run}
+        before = {k: sp[k].canonical() for k in LEPTONS}
+        nion = PS.cell_counts(wl.species["ion"], n_cells)
+        pc = sum(PS.pairs_per_cell(PS.cell_counts(before[k], n_cells), nion) for k in LEPTONS)
+        pairs += PS.by_state(pc, state, n_states)
+        e0, q0, qa0 = energy_charge(before)
+        oled = np.zeros((n_cells, 2))
+        _, ost = orc.step(T, n_cells, wl.material_of_cell, sp["em"], sp["ep"], sp["ph"], sp["ion"], wl.ion_mass,
+                          wl.dt, wl.seed, s, ledger=oled)
+        assert ost["rc"] == 0
+        rec["oracle"]["pairs_total"].append(sum(ost["pairs"]))
+        assert sum(ost["pairs"]) == int(pc.sum()), "pair count of the host bookkeeping"
+        after_o = {k: sp[k].canonical() for k in LEPTONS}
+        ko = PS.event_keys([after_o[k] for k in LEPTONS], s)
+        events += np.bincount(state[PS.key_cell(ko)], minlength=n_states)
+        e1, q1, _ = energy_charge(after_o)
+        rec["oracle"]["de"][s] = PS.rel(e1, e0)
+        rec["oracle"]["dq"][s] = np.abs(q1 - q0) / qa0
+        kk, pk = PS.photon_energies(after_o["ph"], s)
+        sk = state[PS.key_cell(pk >> np.uint64(1))]
+        for m in range(n_states):
+            k_orc[m].append(kk[sk == m])
+
+        for lab, prec in (("fp64", pcc.FP64_PLAIN), ("fp32", pcc.FP32_BATCHED)):
+            dev = {}
+            for k in LEPTONS:
+                n = len(before[k]["w"])
+                dsp = pcc.DeviceSpecies.empty(n_cells, 2 * n + 96 * n_cells)
+                if n:
+                    pcc.bin(ctx, pcc.particles_to_device(before[k]), n_cells, dsp, slack_abs=96, slack_rel=1.0)
+                else:
+                    pcc.bin(ctx, {"n": 0, "ux": None, "uy": None, "uz": None, "w": None, "pid": None, "cell": None},
+                            n_cells, dsp, slack_abs=96, slack_rel=1.0)
+                dev[k] = dsp
+            ledger = torch.zeros((n_cells, 4), dtype=torch.float32, device="cuda")
+            ctx.read_status()
+            pcc.collide(ctx, n_cells, mat, wl.ion_mass, dev["em"], dev["ep"], dev["ph"], ion, wl.dt, wl.seed, s,
+                        precision=prec, ledger=ledger)
+            for k in LEPTONS:
+                pcc.append_secondaries(ctx, n_cells, dev[k])
+            status, stats = ctx.read_status()
+            assert status & pcc.ST_CAPACITY == 0, (lab, s)
+            r = rec[lab]
+            r["status"].append((status, ost["status"]))
+            r["pairs_total"].append(sum(stats["pairs"]))
+            after_g = {k: dev[k].live_host() for k in LEPTONS}
+            kg = PS.event_keys([after_g[k] for k in LEPTONS], s)
+            diff = np.setxor1d(kg, ko)
+            r["mism"] += np.bincount(state[PS.key_cell(diff)], minlength=n_states)
+            bad_cell = np.zeros(n_cells, bool)
+            bad_cell[PS.key_cell(diff)] = True
+            # photons of events both sides made: a relative energy difference
+            # above 1e-4 is a sampling decision (row pick or CDF column) taken
+            # the other way near its threshold, not rounding
+            both = np.intersect1d(kg, ko)
+            kgm, pg = PS.photon_energies(after_g["ph"], s, keys=both)
+            kom, po = PS.photon_energies(after_o["ph"], s, keys=both)
+            assert np.array_equal(pg, po)
+            cm = state[PS.key_cell(pg >> np.uint64(1))]
+            kerr = PS.rel(kgm, kom)
+            flip = kerr > 1e-4
+            r["flips"] += np.bincount(cm[flip], minlength=n_states)
+            r["kerr_all"].append(kerr)
+            np.maximum.at(r["kerr"], cm[~flip], kerr[~flip])
+            bad_cell[PS.key_cell(pg[flip] >> np.uint64(1))] = True
+            led = ledger.cpu().numpy().astype(np.float64)
+            lg = np.stack([led[:, 0] - led[:, 1], led[:, 2] - led[:, 3]], 1)
+            for m in range(n_states):
+                ok = (state == m) & ~bad_cell
+                for col in range(2):
+                    o = oled[ok, col]
+                    nz = o > 0
+                    if nz.any():
+                        r["led_err"][m, col] = max(r["led_err"][m, col],
+                                                   float(np.max(np.abs(lg[ok, col][nz] / o[nz] - 1.0))))
+            kga, pga = PS.photon_energies(after_g["ph"], s)
+            ca = state[PS.key_cell(pga >> np.uint64(1))]
+            for m in range(n_states):
+                r["k_match"][m].append(kgm[cm == m])
+                k_orc_match[lab][m].append(kom[cm == m])
+                r["k"][m].append(kga[ca == m])
+            e1g, q1g, _ = energy_charge(after_g)
+            r["de"][s] = PS.rel(e1g, e0)
+            r["dq"][s] = np.abs(q1g - q0) / qa0
+
+    from scipy.stats import ks_2samp
+    ko_all = [np.concatenate(v) for v in k_orc]
+    for lab in labels:
+        r = rec[lab]
+        r["ks_p"] = np.ones(n_states)
+        for m in range(n_states):
+            a, b = np.concatenate(r["k_match"][m]), np.concatenate(k_orc_match[lab][m])
+            if len(b):
+                r["m1"][m] = abs(a.mean() / b.mean() - 1.0)
+                r["m2"][m] = abs((a * a).mean() / (b * b).mean() - 1.0)
+            ga = np.concatenate(r["k"][m])
+            if len(ga) and len(ko_all[m]):
+                r["ks_p"][m] = ks_2samp(ga, ko_all[m]).pvalue
+
+    # FP32 ln-sigma copies (what the batched kernels read) against the oracle's FP64 sigma
+    tab = np.zeros((n_states, 2))
+    for m in range(n_states):
+        for col, key in enumerate(("brems_sigma", "bh_sigma")):
+            g, o = gt[key][m], getattr(T, key)[m]
+            pos = o > 0
+            s32 = np.exp(np.log(g[pos]).astype(np.float32).astype(np.float64))
+            tab[m, col] = float(np.max(np.abs(s32 / o[pos] - 1.0))) if pos.any() else 0.0
+    out = {"wl": wl, "rec": rec, "pairs": pairs, "events": events, "table": tab, "screening": gt["screening"]}
+    _write_table(out)
+    yield out
     ctx.close()
 
 
-def secondaries(d):
-    p = d["pid"]
-    return set(p[(p >> np.uint64(63)) == 1].tolist())
+def _write_table(st):
+    wl, rec, tab = st["wl"], st["rec"], st["table"]
+    rows = []
+    for m, mt in enumerate(wl.materials):
+        LD, LTF = st["screening"][m][1], st["screening"][m][0]
+        f32, f64, o = rec["fp32"], rec["fp64"], rec["oracle"]
+        rows.append([
+            f"{'Ta' if mt.Z == 73 else 'Al'} {mt.Zstar:g}", f"{mt.T_e:g}", f"{LD / LTF:.3g}",
+            f"{st['pairs'][m]:.3g}", f"{st['events'][m]:.0f}", f"{tab[m, 0]:.1e} / {tab[m, 1]:.1e}",
+            f"{f32['mism'][m]:.0f} ({f32['mism'][m] / st['pairs'][m]:.1e})",
+            f"{f32['flips'][m]:.0f}", f"{f32['kerr'][m]:.1e}",
+            f"{f32['led_err'][m, 0]:.1e} / {f32['led_err'][m, 1]:.1e}",
+            f"{f32['m1'][m]:.1e} / {f32['m2'][m]:.1e}", f"{f32['ks_p'][m]:.2f}",
+            f"{f32['de'][:, m].max():.1e} / {f32['dq'][:, m].max():.1e}",
+            f"{f64['mism'][m]:.0f} / {f64['flips'][m]:.0f}", f"{f64['kerr'][m]:.1e}",
+            f"{f64['led_err'][m, 0]:.1e} / {f64['led_err'][m, 1]:.1e}",
+            f"{f64['m1'][m]:.1e} / {f64['m2'][m]:.1e}",
+            f"{f64['de'][:, m].max():.1e} / {f64['dq'][:, m].max():.1e}",
+            f"{o['de'][:, m].max():.1e} / {o['dq'][:, m].max():.1e}",
+        ])
+    header = ["state (Z*)", "T_e eV", "L_D/L_TF", "pairs", "events", "FP32 table err Brems / BH",
+              "FP32 differing events (per pair)", "FP32 sampling flips", "FP32 photon k err",
+              "FP32 ledger err E / W", "FP32 <k> / <k^2> err", "FP32 KS p",
+              "FP32 drift E / q", "FP64 differing / flips", "FP64 photon k err", "FP64 ledger err E / W",
+              "FP64 <k> / <k^2> err",
+              "FP64 drift E / q", "oracle drift E / q"]
+    text = PS.markdown_table(header, rows)
+    for lab in ("fp32", "fp64"):
+        ka = np.concatenate(rec[lab]["kerr_all"])
+        q = np.quantile(ka, [0.5, 0.99, 0.9999, 1.0])
+        text += (f"\n\n{lab}: relative photon-energy difference over {len(ka)} photons of matched events: "
+                 f"median {q[0]:.1e}, 99% {q[1]:.1e}, 99.99% {q[2]:.1e}, max {q[3]:.1e}; "
+                 f"above 1e-5: {int((ka > 1e-5).sum())}, above 1e-4: {int((ka > 1e-4).sum())}")
+    print("\n" + text)
+    path = os.environ.get("PCC_PRECISION_TABLE")
+    if path:
+        with open(path, "w") as f:
+            f.write(text + "\n")
 
 
-def photon_energies(d):
-    p = d["pid"]
-    m = (p >> np.uint64(63)) == 1
-    return np.sqrt(d["ux"][m].astype(np.float64) ** 2 + d["uy"][m] ** 2 + d["uz"][m] ** 2)
+def test_bookkeeping_matches_counters(pcc, study):
+    """The host pair counts equal both GPU paths' counters, every step."""
+    rec = study["rec"]
+    assert rec["fp64"]["pairs_total"] == rec["oracle"]["pairs_total"]
+    assert rec["fp32"]["pairs_total"] == rec["oracle"]["pairs_total"]
+    for lab in ("fp64", "fp32"):
+        for g, o in rec[lab]["status"]:
+            assert g == o, (lab, g, o)
 
 
-def test_fp32_table_copies(pcc, study):
-    """The FP32 path reads ln sigma rounded to float32: relative error of
-    sigma = exp(|ln sigma| 2^-24) - 1 <= ~4e-6, inside the 1e-5 bound."""
-    gt = study["gpu_tables"]
-    worst = 0.0
-    for key in ("brems_sigma", "bh_sigma"):
-        s = gt[key]
-        pos = s > 0
-        ln32 = np.log(s[pos]).astype(np.float32).astype(np.float64)
-        worst = max(worst, float(np.max(np.abs(np.exp(ln32) / s[pos] - 1.0))))
-    print(f"\n[precision] FP32 ln-sigma table copies: max relative error of sigma {worst:.2e}")
-    assert worst <= 1e-5
+def test_per_state_sample_size(pcc, study):
+    """Each state sees enough pairs that a differing-event bound of 1e-5
+    per pair allows at least three events."""
+    assert study["pairs"].min() >= 3e5
+    assert study["events"].min() >= 1000
 
 
-def test_fp64_gpu_path_reproduces_oracle(pcc, study):
-    r, o = study["runs"]["fp64"], study["orc"]
-    for s in range(STEPS):
-        assert r["stats"][s]["pairs"] == [int(v) for v in o["stats"][s]["pairs"]]
-        assert r["stats"][s]["created"] == [int(v) for v in o["stats"][s]["created"]]
-        assert r["status"][s] == o["stats"][s]["status"]
-    for k in ("em", "ep", "ph"):
-        g, c = r["final"][k], o["final"][k]
-        assert np.array_equal(g["pid"], c["pid"]), k
-        for f in ("ux", "uy", "uz"):
-            np.testing.assert_allclose(g[f], c[f], rtol=2e-6, atol=1e-6, err_msg=f"{k}.{f}")
-    np.testing.assert_allclose(r["ledger"], o["ledger"], rtol=2e-6, atol=1e-30)
+def test_fp32_table_copies_per_state(pcc, study):
+    """float32 rounding of ln sigma: |d sigma/sigma| <= |ln sigma| 2^-24 ~ 4e-6,
+    plus the GPU-vs-oracle FP64 table difference (1e-7)."""
+    assert study["table"].max() <= 1e-5
 
 
-def test_fp32_decisions_ledgers_spectra(pcc, study):
-    r, o = study["runs"]["fp32"], study["orc"]
-    pairs = sum(o["stats"][0]["pairs"])
-    mism = sum(len(secondaries(r["first"][k]) ^ secondaries(o["first"][k])) for k in ("em", "ep", "ph"))
-    created = sum(o["stats"][0]["created"])
-    # ledgers of cells whose events match exactly after all steps
-    same = np.ones(study["wl"].n_cells, bool)
-    for k in ("em", "ep", "ph"):
-        g, c = r["final"][k], o["final"][k]
-        sg = {(int(cl), int(p)) for cl, p in zip(g["cell"], g["pid"]) if p >> np.uint64(63)}
-        so = {(int(cl), int(p)) for cl, p in zip(c["cell"], c["pid"]) if p >> np.uint64(63)}
-        for cl, _ in sg ^ so:
-            same[cl] = False
-    lg, lo = r["ledger"][same, 0], o["ledger"][same, 0]
-    nz = lo > 0
-    led_err = float(np.max(np.abs(lg[nz] / lo[nz] - 1.0))) if nz.any() else 0.0
-    kg, ko = photon_energies(r["final"]["ph"]), photon_energies(o["final"]["ph"])
-    m1 = abs(kg.mean() / ko.mean() - 1.0)
-    m2 = abs((kg ** 2).mean() / (ko ** 2).mean() - 1.0)
-    print(f"\n[precision] FP32 vs FP64 oracle: {mism} differing secondaries in {pairs} pairs "
-          f"({mism / pairs:.1e} per pair; {created} events), ledger max rel err {led_err:.1e} "
-          f"({int(same.sum())} cells), photon spectrum moments rel err {m1:.1e} / {m2:.1e}")
-    assert mism <= max(2, 1e-5 * pairs)
-    assert led_err <= 1e-5
-    assert m1 <= 1e-3 and m2 <= 2e-3
+def test_fp64_gpu_path_per_state(pcc, study):
+    r = study["rec"]["fp64"]
+    assert r["mism"].max() == 0 and r["flips"].max() == 0
+    assert r["kerr"].max() <= 1e-6             # float32 storage of the photon momenta
+    assert r["led_err"].max() <= 2e-6          # float32 storage of the ledger
+    assert r["m1"].max() <= 1e-6 and r["m2"].max() <= 2e-6
+    assert r["de"].max() <= 1e-6 and r["dq"].max() <= 1e-6
 
 
-def test_conservation_drift(pcc, study):
-    """Ions at rest: every event conserves energy and charge exactly in exact
-    arithmetic; what remains is the float32 storage of the momenta (2^-24
-    relative per stored component of each changed particle)."""
-    lines = []
-    for label in ("fp64", "fp32"):
-        eq = study["runs"][label]["eq"]
-        de = [abs(eq[s + 1][0] - eq[s][0]) / eq[s][0] for s in range(STEPS)]
-        dq = [abs(eq[s + 1][1] - eq[s][1]) / max(abs(eq[s][1]), 1.0) for s in range(STEPS)]
-        lines.append(f"{label}: energy drift/step max {max(de):.1e}, charge drift/step max {max(dq):.1e}")
-        assert max(de) <= 1e-6, label
-        assert max(dq) <= 1e-6, label
-    print("\n[precision] " + "; ".join(lines))
+def test_fp32_path_per_state(pcc, study):
+    r, pairs = study["rec"]["fp32"], study["pairs"]
+    bound = np.maximum(2.0, 1e-5 * pairs)
+    assert np.all(r["mism"] <= bound), r["mism"]
+    # sampling decisions taken the other way: as rare as the accept flips
+    assert np.all(r["flips"] <= np.maximum(2.0, 1e-5 * study["events"])), r["flips"]
+    assert r["kerr"].max() <= 2e-5
+    assert r["led_err"].max() <= 1e-5
+    assert r["m1"].max() <= 2e-5 and r["m2"].max() <= 4e-5
+    assert r["ks_p"].min() > 0.01
+    assert r["de"].max() <= 1e-6 and r["dq"].max() <= 1e-6
