@@ -351,6 +351,7 @@ def run_gpu(args):
                    "photons": before["ph"], "positrons": before["ep"], "precision": args.precision,
                    "l2": "inputs larger than L2 (about 7 GB of particle records), no flush",
                    "timed": f"{K} steps in one CUDA graph", "schedule": schedule and list(schedule["schedule"]),
+                   "scan_classes": {str(g): ctx.scan_classes(g) for g in (0, 1, 2)},
                    "schedule_ms": schedule and schedule["ms"],
                    "parallelism": f"replicas{world}"},
         "events_per_s": events_all / (ms_max * 1e-3),

@@ -231,6 +231,23 @@ int pcc_collide(pcc_ctx *ctx, const pcc_cells *cells, pcc_species *em, pcc_speci
  * on this context.  PCC_E_INVALID outside these ranges. */
 int pcc_set_schedule(pcc_ctx *ctx, int min_blocks_per_sm, int blocks_per_sm);
 
+/* Lane groups of the batched scan (no counterpart in the paper; a
+ * performance setting).  The random streams do not depend on it; it changes
+ * only the order of the FP32 sums of a cell's weights, hence at most the
+ * last bit of the pair coefficient and with it, rarely, a decision within
+ * float rounding of its threshold.  Cells are sorted into
+ * size classes, two per octave of N_pair = max(N_p, N_t): class 0 is
+ * N_pair = 1, and with b the bit length of N_pair, class 2(b-1) holds
+ * [2^(b-1), 1.5 2^(b-1)) and class 2(b-1)+1 holds [1.5 2^(b-1), 2^b); 34
+ * classes.  For group (0 e-, 1 e+, 2 photons), thresholds[4] = {warp, g16,
+ * g8, g4}: cells of class >= warp take a whole warp, [g16, warp) 16 lanes,
+ * [g8, g16) 8 lanes, [g4, g8) 4 lanes and the smaller ones 2 lanes.
+ * Requires 0 <= g4 <= g8 <= g16 <= warp <= 34 (PCC_E_INVALID otherwise).
+ * Applies to later pcc_collide calls on this context.  pcc_get_scan_classes
+ * reads the current setting (host int[4]). */
+int pcc_set_scan_classes(pcc_ctx *ctx, int group, const int *thresholds);
+int pcc_get_scan_classes(const pcc_ctx *ctx, int group, int *thresholds);
+
 /* Fault injection (no counterpart in the paper): the bounded waits of the
  * batched kernels (the mbarrier of the bulk copy that stages the ln sigma
  * rows in shared memory) give up after `polls` polls instead of 4194304,

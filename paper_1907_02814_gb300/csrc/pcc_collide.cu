@@ -782,7 +782,9 @@ __global__ void __launch_bounds__(128) collide_plain_kernel(const __grid_constan
 // round-robin, so each warp receives a similar share of large and small
 // cells.
 constexpr int kBatchedThreads = 256;
-constexpr int kClasses = 18;
+// Size classes of the cells, two per octave of N_pair = max(N_p, N_t)
+// (see size_class).
+constexpr int kClasses = 34;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -792,16 +794,22 @@ struct CellList {
     int* cursor;     // [kClasses] (unused)
     int* bh;         // [kClasses][nblk] per-block class counts, then their offsets
     int nblk;        // blocks of kClassBlock cells
+    int thr[4];      // scan lane groups: classes >= thr[0] a whole warp, [thr[1], thr[0]) 16 lanes,
+                     // [thr[2], thr[1]) 8, [thr[3], thr[2]) 4, below 2 (pcc_set_scan_classes)
 };
 
 constexpr int kClassBlock = 1024;                 // cells per class-sort block
 constexpr int kClassSmemMax = 200 * 1024;         // offsets scanned in shared memory up to this size
 
+// Class of a cell with N_pair = max(N_p, N_t) pairs: with b the bit length
+// of N_pair, class 2(b - 1) for N_pair in [2^(b-1), 1.5 2^(b-1)) and
+// 2(b - 1) + 1 for [1.5 2^(b-1), 2^b); N_pair = 1 is class 0.
 __device__ __forceinline__ int size_class(int np, int nt)
 {
     const int n = np > nt ? np : nt;
     const int b = 32 - __clz(n);
-    return b < kClasses ? b : kClasses - 1;
+    const int k = b >= 2 ? 2 * (b - 1) + ((n >> (b - 2)) & 1) : 0;
+    return k < kClasses ? k : kClasses - 1;
 }
 
 // The class sorts of the three groups {e-, e+, photon} against the ions,
@@ -1093,7 +1101,11 @@ __device__ __forceinline__ void flag_cell(const Queue& Q, int cell)
 }
 
 // Acceptance bounds of the group at this coefficient, as thresholds on the
-// accept words: a pair can be accepted only if r <= floor(2^32 b).
+// accept words: a pair can be accepted only if r <= floor(2^32 b).  The
+// per-material bounds carry the ion-motion factor 1 + |beta_i| at its
+// largest value 2; for the electrons the scan passes coef times
+// (1 + max |beta_i|)/2 of the cell, which halves their candidates where the
+// ions are slow.
 template <int GROUP>
 __device__ __forceinline__ void bound_thresholds(const StepArgs& a, int mat, float coef, uint32_t& k1, uint32_t& k2)
 {
@@ -1157,6 +1169,14 @@ __device__ __forceinline__ T group_sum(T v)
 {
 #pragma unroll
     for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ float group_max(float v)
+{
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -1273,13 +1293,25 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
         const bool caseA = Np >= Nt;
         // ---- sums (the first G weights of each list were prefetched)
         const float w0 = __shfl_sync(kFull, tw0, 0, G);
-        float sp = 0.f, st = 0.f, sf = 0.f;
+        float sp = 0.f, st = 0.f, sf = 0.f, b2 = 0.f;
         bool uni = true;
+        // the ion weights, and for the electrons the largest ion speed of the
+        // cell for the bound (beta^2 = u^2/(1 + u^2); non-finite momenta give
+        // beta = 1).  Electrons are most of the pairs: there the momentum
+        // loads pay for themselves in fewer candidates; for positrons and
+        // photons they do not, and the bound keeps 1 + |beta_i| <= 2.
 #pragma unroll 4
         for (uint32_t s = gl; s < Nt; s += G) {
             const float wt = s < (uint32_t)G ? tw0 : I.w[t0 + s];
             st += wt;
             uni &= (wt == w0);
+            if constexpr (GROUP == kGroupEm) {
+                const float ux = I.ux[t0 + s], uy = I.uy[t0 + s], uz = I.uz[t0 + s];
+                const float u2 = ux * ux + uy * uy + uz * uz;
+                b2 = fmaxf(b2, isfinite(u2) ? __fdividef(u2, 1.f + u2) : 1.f);
+            } else {
+                b2 = 1.f;
+            }
         }
         if (caseA) {
 #pragma unroll 4
@@ -1316,31 +1348,41 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
             }
         }
         const float coef = __fdividef(n_p, n_pt) * n_t * a.f_cdt;
+        // 1 + max |beta_i| of the cell, rounded up past the few ulps of its
+        // float evaluation (2 for positrons and photons)
+        const float bfac = GROUP == kGroupEm ? fminf((1.f + sqrtf(fminf(group_max<G>(b2), 1.f))) * (1.f + 0x1p-20f), 2.f)
+                                             : 2.f;
         uint32_t k1 = 0, k2 = 0;
-        if (active) bound_thresholds<GROUP>(a, mat, coef, k1, k2);
+        if (active) bound_thresholds<GROUP>(a, mat, coef * (0.5f * bfac), k1, k2);
         uint32_t ncand = 0;   // candidates of this lane's cell (uniform over its group)
         // ---- cells with N_p >= N_t: one pair per projectile slot
         const uint32_t itA = active && caseA ? (Np + 2 * G - 1) / (2 * G) : 0u;
         const uint32_t nitA = G == 32 ? itA : __reduce_max_sync(kFull, itA);
         const uint32_t tag0 = stream_tag(GROUP, kAccept, 0);
+        uint32_t mine = 0;   // candidates of this lane
         for (uint32_t it = 0; it < nitA; ++it) {
             const uint32_t base = it * (2 * G);
             const Philox4 ph = draw_k((base >> 1) + gl, (uint32_t)cell, step32, tag0, a.keys);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t s = base + 2 * gl + h;
-                const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
-                const bool cand = (G == 32 || it < itA) && s < Np && (r1 <= k1 || r2 <= k2);
-                const unsigned m = __ballot_sync(kFull, cand);
-                if (cand) wb[sw.nb + __popc(m & below)] = make_uint2((uint32_t)cell, s);
-                sw.nb += __popc(m);
-                ncand += __popc(m & gmask);
-            }
-            if (sw.nb > kWarpBuf - 64) {   // flush the staging buffer to the flat queue
-                flush_staged(Q, wb, sw.nb, bacc, lane);
-                sw.nb = 0;
+            const bool live = G == 32 || it < itA;
+            const uint32_t s0 = base + 2 * gl;
+            const bool c0 = live && s0 < Np && (ph.v[0] <= k1 || ph.v[1] <= k2);
+            const bool c1 = live && s0 + 1 < Np && (ph.v[2] <= k1 || ph.v[3] <= k2);
+            // most iterations of small cells have no candidate in the warp
+            if (__any_sync(kFull, c0 || c1)) {
+                const unsigned m0 = __ballot_sync(kFull, c0);
+                if (c0) wb[sw.nb + __popc(m0 & below)] = make_uint2((uint32_t)cell, s0);
+                sw.nb += __popc(m0);
+                const unsigned m1 = __ballot_sync(kFull, c1);
+                if (c1) wb[sw.nb + __popc(m1 & below)] = make_uint2((uint32_t)cell, s0 + 1);
+                sw.nb += __popc(m1);
+                mine += (uint32_t)c0 + (uint32_t)c1;
+                if (sw.nb > kWarpBuf - 64) {   // flush the staging buffer to the flat queue
+                    flush_staged(Q, wb, sw.nb, bacc, lane);
+                    sw.nb = 0;
+                }
             }
         }
+        ncand = group_sum<G>(mine);
         // ---- cells with N_p < N_t.  Draw units (pass m, slot pair q): unit
         // i = m Qn + q covers slots 2q and 2q+1 of pass m, i.e. pairs
         // j = s + m N_p.  A group's lanes take consecutive units, so each
@@ -1382,15 +1424,6 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
     }
 }
 
-// Lane-group width by size class (class k: N_pair in [2^(k-1), 2^k)), per
-// group: classes from `warp` up take a whole warp, [g16, warp) 16 lanes,
-// [g8, g16) 8 lanes, [g4, g8) 4 lanes, and the smaller ones 2 lanes.
-// Chosen by timing each group on the 2^20-cell batched Cu workload.
-template <int GROUP> struct ScanClass;
-template <> struct ScanClass<kGroupEm> { static constexpr int warp = 11, g16 = 10, g8 = 8, g4 = 1; };
-template <> struct ScanClass<kGroupEp> { static constexpr int warp = 7, g16 = 7, g8 = 4, g4 = 1; };
-template <> struct ScanClass<kGroupPh> { static constexpr int warp = 10, g16 = 9, g8 = 8, g4 = 7; };
-
 // Scan: for each cell, the sums n_p, n_t, n_pt of Sec. III.A, the
 // coefficient, and the accept uniforms of every pair against the
 // per-material bounds.  Pairs at or above the bounds are rejected here,
@@ -1417,10 +1450,10 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
     int e32 = 0, e16 = 0, e8 = 0, e4 = 0, e2 = 0;
     for (int k = kClasses - 1; k >= 0; --k) {
         const int h = L.hist[k];
-        if (k >= ScanClass<GROUP>::warp) e32 += h;
-        else if (k >= ScanClass<GROUP>::g16) e16 += h;
-        else if (k >= ScanClass<GROUP>::g8) e8 += h;
-        else if (k >= ScanClass<GROUP>::g4) e4 += h;
+        if (k >= L.thr[0]) e32 += h;
+        else if (k >= L.thr[1]) e16 += h;
+        else if (k >= L.thr[2]) e8 += h;
+        else if (k >= L.thr[3]) e4 += h;
         else e2 += h;
     }
     e16 += e32;
@@ -1855,6 +1888,7 @@ static CellList list_of(pcc_ctx* ctx, int group)
     L.cursor = L.hist + kClasses;
     L.nblk = (int)((n + kClassBlock - 1) / kClassBlock);
     L.bh = ctx->lists + hist_off(n) + 6 * kClasses + 8 + (size_t)group * kClasses * L.nblk;
+    for (int i = 0; i < 4; ++i) L.thr[i] = ctx->scan_thr[group][i];
     return L;
 }
 
@@ -1993,6 +2027,32 @@ extern "C" int pcc_set_wait_limit(pcc_ctx* ctx, int polls)
         return PCC_E_INVALID;
     }
     ctx->wait_polls = polls;
+    return PCC_OK;
+}
+
+extern "C" int pcc_set_scan_classes(pcc_ctx* ctx, int group, const int* thresholds)
+{
+    if (!ctx || group < 0 || group > 2 || !thresholds) {
+        set_error("pcc_set_scan_classes: invalid argument");
+        return PCC_E_INVALID;
+    }
+    const int* t = thresholds;
+    if (!(0 <= t[3] && t[3] <= t[2] && t[2] <= t[1] && t[1] <= t[0] && t[0] <= kClasses)) {
+        set_error("pcc_set_scan_classes: thresholds must satisfy 0 <= g4 <= g8 <= g16 <= warp <= " +
+                  std::to_string(kClasses));
+        return PCC_E_INVALID;
+    }
+    for (int i = 0; i < 4; ++i) ctx->scan_thr[group][i] = t[i];
+    return PCC_OK;
+}
+
+extern "C" int pcc_get_scan_classes(const pcc_ctx* ctx, int group, int* thresholds)
+{
+    if (!ctx || group < 0 || group > 2 || !thresholds) {
+        set_error("pcc_get_scan_classes: invalid argument");
+        return PCC_E_INVALID;
+    }
+    for (int i = 0; i < 4; ++i) thresholds[i] = ctx->scan_thr[group][i];
     return PCC_OK;
 }
 

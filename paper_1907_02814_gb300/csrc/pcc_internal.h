@@ -44,6 +44,11 @@ struct pcc_ctx {
     void* queue_b = nullptr;       // candidate queue over target slots (N_p < N_t cells)
     size_t queue_b_cap = 0;
     int minb = 4;                  // register budget: minimum resident blocks per SM
+    // lane groups of the batched scan per group (e-, e+, photons): size
+    // classes (two per octave of N_pair) from which a cell takes a whole
+    // warp, 16, 8 or 4 lanes (below: 2).  Chosen by timing on the 2^20-cell
+    // batched Cu workload; the autotuner may replace them.
+    int scan_thr[3][4] = {{20, 18, 14, 0}, {12, 12, 6, 0}, {18, 16, 14, 12}};
     int blocks_per_sm = 0;         // persistent grid cap (0: as many as fit)
     bool class_smem_ready = false; // large shared memory enabled for the class-sort offsets
     int wait_polls = 1 << 22;      // bounded waits give up after this many polls (fault injection: 0)

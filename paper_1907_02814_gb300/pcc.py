@@ -79,6 +79,8 @@ EXPORTS = {
                               C.POINTER(Species), C.c_double, C.c_uint64, C.c_uint64, C.c_uint, C.c_int, _vp, _vp]),
     "pcc_append_secondaries": (C.c_int, [_vp, C.c_int, C.POINTER(Species), _vp]),
     "pcc_set_schedule": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "pcc_set_scan_classes": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
+    "pcc_get_scan_classes": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "pcc_set_wait_limit": (C.c_int, [_vp, C.c_int]),
     "pcc_pairing": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.POINTER(Species), C.c_int, C.c_uint64,
                               C.c_uint64, _vp, _vp, _vp]),
@@ -201,6 +203,17 @@ class Context:
 
     def set_schedule(self, min_blocks_per_sm=4, blocks_per_sm=0):
         _check(self.lib.pcc_set_schedule(self.h, int(min_blocks_per_sm), int(blocks_per_sm)), "pcc_set_schedule")
+
+    def set_scan_classes(self, group, thresholds):
+        """Lane groups of the batched scan for group 0 (e-), 1 (e+) or 2
+        (photons): size classes {warp, g16, g8, g4} (see pcc.h)."""
+        arr = (C.c_int * 4)(*[int(v) for v in thresholds])
+        _check(self.lib.pcc_set_scan_classes(self.h, int(group), arr), "pcc_set_scan_classes")
+
+    def scan_classes(self, group):
+        arr = (C.c_int * 4)()
+        _check(self.lib.pcc_get_scan_classes(self.h, int(group), arr), "pcc_get_scan_classes")
+        return [arr[i] for i in range(4)]
 
     def set_wait_limit(self, polls=1 << 22):
         """Fault injection: bounded waits give up after `polls` polls (0: at once)."""

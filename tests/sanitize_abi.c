@@ -86,6 +86,11 @@ int main(void)
            "pcc_collide");
     expect(pcc_set_schedule(NULL, 1, 1), PCC_E_INVALID, "pcc_set_schedule");
     expect(pcc_set_wait_limit(NULL, 1), PCC_E_INVALID, "pcc_set_wait_limit");
+    {
+        int thr[4] = {20, 18, 14, 0};
+        expect(pcc_set_scan_classes(NULL, 0, thr), PCC_E_INVALID, "pcc_set_scan_classes");
+        expect(pcc_get_scan_classes(NULL, 0, thr), PCC_E_INVALID, "pcc_get_scan_classes");
+    }
     expect(pcc_append_secondaries(NULL, 1, &sp, NULL), PCC_E_INVALID, "pcc_append_secondaries");
     expect(pcc_pairing(NULL, 1, &sp, &sp, 0, 1, 0, iv, iv, NULL), PCC_E_INVALID, "pcc_pairing");
     expect(pcc_totals(NULL, 1, &sp, 0, d, NULL), PCC_E_INVALID, "pcc_totals");

@@ -53,6 +53,9 @@ def test_null_arguments_rejected_without_a_device(lib):
     assert L.pcc_tables_build(None, None, 0, None, None) == pcc.PCC_E_INVALID
     assert L.pcc_collide(None, None, None, None, None, None, 1.0, 0, 0, 7, 0, None, None) == pcc.PCC_E_INVALID
     assert b"invalid" in L.pcc_last_error()
+    thr = (ctypes.c_int * 4)(20, 18, 14, 0)
+    assert L.pcc_set_scan_classes(None, 0, thr) == pcc.PCC_E_INVALID
+    assert L.pcc_get_scan_classes(None, 0, thr) == pcc.PCC_E_INVALID
 
 
 def test_status_strings_without_a_device(lib):

@@ -5,6 +5,8 @@ autotuner applies and caches a candidate."""
 import numpy as np
 import pytest
 
+import precision_study as PS
+
 torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
@@ -136,10 +138,65 @@ def test_tune_applies_and_caches(pcc, ctx, tmp_path):
     d = to_device(pcc, ctx, wl)
     before = d["em"].ux.clone()
     path = str(tmp_path / "tune.json")
+    defaults = {g: ctx.scan_classes(g) for g in (0, 1, 2)}
     r = tune.tune(ctx, pcc, torch, wl.n_cells, mat, wl.ion_mass, d, wl.dt, wl.seed, cache_path=path, reps=1)
     assert tuple(r["schedule"]) in tune.CANDIDATES and not r["cached"]
-    assert len(r["ms"]) == len(tune.CANDIDATES) and all(v > 0 for v in r["ms"].values())
+    sched = [k for k in r["ms"] if not k.startswith("classes")]
+    assert len(sched) == len(tune.CANDIDATES) and all(v > 0 for v in r["ms"].values())
+    assert set(r["classes"]) == set(tune.CLASS_GROUPS)
+    for g, t in r["classes"].items():
+        assert tune.valid_classes(t) and ctx.scan_classes(g) == list(t)
     assert torch.equal(d["em"].ux, before)          # trials ran on a scratch copy
+    for g, t in defaults.items():
+        ctx.set_scan_classes(g, t)
     r2 = tune.tune(ctx, pcc, torch, wl.n_cells, mat, wl.ion_mass, d, wl.dt, wl.seed, cache_path=path)
     assert r2["cached"] and tuple(r2["schedule"]) == tuple(r["schedule"])
+    assert {g: list(t) for g, t in r2["classes"].items()} == {g: list(t) for g, t in r["classes"].items()}
+    assert all(ctx.scan_classes(g) == list(t) for g, t in r["classes"].items())
     ctx.set_schedule(4, 0)
+    for g, t in defaults.items():
+        ctx.set_scan_classes(g, t)
+
+
+def test_scan_classes_keep_the_events(pcc, ctx):
+    """The lane-group setting of the scan is a performance choice: whole
+    warps for every cell, 2-lane groups for every cell, and the default give
+    the same pairs and the same events (it changes only the order of a
+    cell's FP32 weight sums, so at most a decision within float rounding of
+    its threshold could differ); bad thresholds are rejected."""
+    wl = workload(n_cells=128, seed=14)
+    tables(pcc, ctx, wl)
+    mat = torch.as_tensor(wl.material_of_cell, device="cuda")
+    defaults = {g: ctx.scan_classes(g) for g in (0, 1, 2)}
+    out = []
+    try:
+        for thr in (None, [0, 0, 0, 0], [34, 34, 34, 34], [9, 7, 5, 3]):
+            if thr is not None:
+                for g in (0, 1, 2):
+                    ctx.set_scan_classes(g, thr)
+            d = to_device(pcc, ctx, wl)
+            ctx.read_status()
+            for s in range(2):
+                pcc.collide(ctx, wl.n_cells, mat, wl.ion_mass, d["em"], d["ep"], d["ph"], d["ion"], wl.dt, wl.seed,
+                            s, precision=pcc.FP32_BATCHED)
+                for k in ("em", "ep", "ph"):
+                    pcc.append_secondaries(ctx, wl.n_cells, d[k])
+            st, stats = ctx.read_status()
+            out.append((st, stats, {k: d[k].live_host() for k in ("em", "ep", "ph")}))
+    finally:
+        for g, t in defaults.items():
+            ctx.set_scan_classes(g, t)
+    st0, stats0, p0 = out[0]
+    assert st0 == 0 and sum(stats0["created"]) > 10
+    keys0 = PS.event_keys_all([p0[k] for k in ("em", "ep", "ph")])
+    for st, stats, p in out[1:]:
+        assert st == st0 and stats["pairs"] == stats0["pairs"]
+        keys = PS.event_keys_all([p[k] for k in ("em", "ep", "ph")])
+        assert len(np.setxor1d(keys, keys0)) <= 2
+        assert abs(sum(stats["candidates"]) - sum(stats0["candidates"])) <= 4
+    for bad in ([10, 12, 4, 0], [35, 2, 1, 0], [4, 3, 2, -1]):
+        with pytest.raises(pcc.PccError, match="thresholds"):
+            ctx.set_scan_classes(0, bad)
+    with pytest.raises(pcc.PccError):
+        ctx.set_scan_classes(3, [4, 3, 2, 1])
+    assert ctx.scan_classes(0) == defaults[0]
