@@ -821,6 +821,7 @@ struct ClassSort {
     const int* cnt_t;      // ion counts
     int n_cells;
     unsigned run;          // bit g: group g is sorted
+    unsigned* serial;      // collide calls so far (stamps the per-cell ion summaries)
 };
 
 // Counting sort of the cells with both species by decreasing size class,
@@ -832,6 +833,7 @@ struct ClassSort {
 // independently of where it sits in the list.
 __global__ void class_hist_kernel(const __grid_constant__ ClassSort S)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *S.serial += 1u;   // a new call: earlier summaries go stale
     __shared__ int h[3][kClasses];
     for (int i = threadIdx.x; i < 3 * kClasses; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
@@ -1005,6 +1007,18 @@ __device__ __forceinline__ uint32_t fast_mod(uint32_t j, uint32_t n, float inv_n
     if (r >= (int)n) r -= (int)n;
     return (uint32_t)r;
 }
+
+// Per-cell summary of the ions written by the electron scan, which reads
+// every ion of its cells anyway, for the positron and photon scans of the
+// same call: x = n_t (the electron scan's FP32 sum), y = w0 (first ion
+// weight), z = 1 + max |beta_i| rounded up (negative when the ion weights are
+// not all w0), w = the call's serial (bits).  A scan whose cell carries
+// another serial (no electrons there, or the electron group did not run in
+// this call) reads the ion weights itself.
+struct IonCache {
+    float4* sum;            // [n_cells]
+    const unsigned* serial; // incremented by the class sort at the start of each call
+};
 
 // Per-cell metadata, loaded one cell ahead by the persistent loop.
 struct CellMeta {
@@ -1246,9 +1260,9 @@ __device__ __forceinline__ void flush_staged(const Queue& Q, const uint2* wb, in
 // Loops that hold ballots run to the largest trip count of the warp's
 // groups, so every collective is reached by all 32 lanes.
 template <int GROUP, int G>
-__device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& L, const Queue& Q, int e0, int e1,
-                                             int t_first, int nwarps, int* tab, uint2* wb, ScanWarp& sw,
-                                             BlockAcc& bacc)
+__device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& L, const Queue& Q, const IonCache& IC,
+                                             int e0, int e1, int t_first, int nwarps, int* tab,
+                                             uint2* wb, ScanWarp& sw, BlockAcc& bacc)
 {
     constexpr int C = 32 / G;
     constexpr unsigned kFull = 0xffffffffu;
@@ -1262,18 +1276,29 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
     const int e_lane = e0 + gi;   // entry of tuple t for this lane: e_lane + t C
     // Two-stage prefetch: the metadata of the tuple after next, and the first
     // G weights of both lists of the next tuple, load while a tuple is scanned.
+    constexpr bool kWriter = GROUP == kGroupEm;   // the electron scan writes the ion summaries
+    const auto first_ion = [&](const CellMeta& m) -> float {
+        return (uint32_t)gl < m.Nt ? I.w[m.t0 + gl] : 0.f;
+    };
+    const auto ion_sum = [&](const CellMeta& m) -> float4 {
+        return (m.cell >= 0 && m.cell < a.n_cells) ? IC.sum[m.cell] : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
     int t = t_first;
     CellMeta next = load_meta(a, P, t < ntup && e_lane + t * C < e1 ? L.list[e_lane + t * C] : -1);
-    float next_tw = (uint32_t)gl < next.Nt ? I.w[next.t0 + gl] : 0.f;
+    float next_tw = kWriter ? first_ion(next) : 0.f;
+    float4 next_is = kWriter ? make_float4(0.f, 0.f, 0.f, 0.f) : ion_sum(next);
     float next_pw = (uint32_t)gl < next.Np ? P.w[next.p0 + gl] : 0.f;
     int t2 = t + nwarps;
     CellMeta next2 = load_meta(a, P, t2 < ntup && e_lane + t2 * C < e1 ? L.list[e_lane + t2 * C] : -1);
     while (t < ntup) {
         const CellMeta cm = next;
-        const float tw0 = next_tw, pw0 = next_pw;   // weights of slot gl of this cell
+        float tw0 = next_tw;
+        const float pw0 = next_pw;   // weights of slot gl of this cell
+        const float4 is = next_is;   // its ion summary (readers)
         t += nwarps;
         next = next2;
-        next_tw = (uint32_t)gl < next.Nt ? I.w[next.t0 + gl] : 0.f;
+        if constexpr (kWriter) next_tw = first_ion(next);
+        else next_is = ion_sum(next);
         next_pw = (uint32_t)gl < next.Np ? P.w[next.p0 + gl] : 0.f;
         t2 = t + nwarps;
         next2 = load_meta(a, P, t2 < ntup && e_lane + t2 * C < e1 ? L.list[e_lane + t2 * C] : -1);
@@ -1291,27 +1316,43 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
             if (!__any_sync(kFull, active)) continue;
         }
         const bool caseA = Np >= Nt;
-        // ---- sums (the first G weights of each list were prefetched)
-        const float w0 = __shfl_sync(kFull, tw0, 0, G);
+        // ---- sums (the first G weights of each list were prefetched).  The
+        // electron scan sums the ion weights and takes the largest ion speed
+        // of the cell for the bound (beta^2 = u^2/(1 + u^2); non-finite
+        // momenta give beta = 1); the other scans take both from the
+        // electron scan's summary when it is from this call, else sum the ion
+        // weights themselves and keep the bound's factor at 2.
+        const bool have = !kWriter && __float_as_uint(is.w) == *IC.serial;
+        if (!kWriter && !have) tw0 = first_ion(cm);
+        // (every collective below runs on all 32 lanes; `have` only selects)
+        const float w0s = __shfl_sync(kFull, tw0, 0, G);
+        const float w0 = have ? is.y : w0s;
         float sp = 0.f, st = 0.f, sf = 0.f, b2 = 0.f;
-        bool uni = true;
-        // the ion weights, and for the electrons the largest ion speed of the
-        // cell for the bound (beta^2 = u^2/(1 + u^2); non-finite momenta give
-        // beta = 1).  Electrons are most of the pairs: there the momentum
-        // loads pay for themselves in fewer candidates; for positrons and
-        // photons they do not, and the bound keeps 1 + |beta_i| <= 2.
+        bool uni = have ? is.z > 0.f : true;
+        if (!have) {
 #pragma unroll 4
-        for (uint32_t s = gl; s < Nt; s += G) {
-            const float wt = s < (uint32_t)G ? tw0 : I.w[t0 + s];
-            st += wt;
-            uni &= (wt == w0);
-            if constexpr (GROUP == kGroupEm) {
-                const float ux = I.ux[t0 + s], uy = I.uy[t0 + s], uz = I.uz[t0 + s];
-                const float u2 = ux * ux + uy * uy + uz * uz;
-                b2 = fmaxf(b2, isfinite(u2) ? __fdividef(u2, 1.f + u2) : 1.f);
-            } else {
-                b2 = 1.f;
+            for (uint32_t s = gl; s < Nt; s += G) {
+                const float wt = s < (uint32_t)G ? tw0 : I.w[t0 + s];
+                st += wt;
+                uni &= (wt == w0);
+                if constexpr (kWriter) {
+                    const float ux = I.ux[t0 + s], uy = I.uy[t0 + s], uz = I.uz[t0 + s];
+                    const float u2 = ux * ux + uy * uy + uz * uz;
+                    b2 = fmaxf(b2, isfinite(u2) ? __fdividef(u2, 1.f + u2) : 1.f);
+                } else {
+                    b2 = 1.f;
+                }
             }
+        }
+        const float st_sum = group_sum<G>(st);
+        const float n_t = have ? is.x : st_sum;
+        // 1 + max |beta_i| of the cell, rounded up past the few ulps of its
+        // float evaluation (2 without the summary in the other scans)
+        const float bmax = group_max<G>(b2);
+        const float bfac = have ? fabsf(is.z) : fminf((1.f + sqrtf(fminf(bmax, 1.f))) * (1.f + 0x1p-20f), 2.f);
+        if constexpr (kWriter) {
+            if (active && gl == 0)
+                IC.sum[cell] = make_float4(n_t, w0, uni ? bfac : -bfac, __uint_as_float(*IC.serial));
         }
         if (caseA) {
 #pragma unroll 4
@@ -1327,7 +1368,7 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
                 sf += fminf(wp, w0) * (float)((Nt - s + Np - 1) / Np);
             }
         }
-        const float n_p = group_sum<G>(sp), n_t = group_sum<G>(st);
+        const float n_p = group_sum<G>(sp);
         float n_pt;
         if constexpr (G == 32) {
             n_pt = __all_sync(kFull, uni) ? warp_sum(sf) : npt_over_pairs<GROUP>(a, P, cell, p0, t0, Np, Nt, tab, lane);
@@ -1348,10 +1389,6 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
             }
         }
         const float coef = __fdividef(n_p, n_pt) * n_t * a.f_cdt;
-        // 1 + max |beta_i| of the cell, rounded up past the few ulps of its
-        // float evaluation (2 for positrons and photons)
-        const float bfac = GROUP == kGroupEm ? fminf((1.f + sqrtf(fminf(group_max<G>(b2), 1.f))) * (1.f + 0x1p-20f), 2.f)
-                                             : 2.f;
         uint32_t k1 = 0, k2 = 0;
         if (active) bound_thresholds<GROUP>(a, mat, coef * (0.5f * bfac), k1, k2);
         uint32_t ncand = 0;   // candidates of this lane's cell (uniform over its group)
@@ -1436,7 +1473,7 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
 // stays in registers.
 template <int GROUP, int MINB>
 __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __grid_constant__ StepArgs a, CellList L,
-                                                                     Queue Q)
+                                                                     Queue Q, IonCache IC)
 {
     __shared__ int scratch[kBatchedThreads / 32][64];
     __shared__ uint2 buf[kBatchedThreads / 32][kWarpBuf];
@@ -1466,15 +1503,19 @@ __global__ void __launch_bounds__(kBatchedThreads, MINB) scan_kernel(const __gri
     // the round-robin continues across segments: a segment's first tuple
     // goes to the warp after the one that took the previous segment's last
     int d = 0;
-    scan_segment<GROUP, 32>(a, L, Q, 0, e32, gw, nwarps, tab, wb, sw, bacc);
+    scan_segment<GROUP, 32>(a, L, Q, IC, 0, e32, gw, nwarps, tab, wb, sw, bacc);
     d = (d + e32) % nwarps;
-    scan_segment<GROUP, 16>(a, L, Q, e32, e16, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw, bacc);
+    scan_segment<GROUP, 16>(a, L, Q, IC, e32, e16, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw,
+                             bacc);
     d = (d + (e16 - e32 + 1) / 2) % nwarps;
-    scan_segment<GROUP, 8>(a, L, Q, e16, e8, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw, bacc);
+    scan_segment<GROUP, 8>(a, L, Q, IC, e16, e8, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw,
+                             bacc);
     d = (d + (e8 - e16 + 3) / 4) % nwarps;
-    scan_segment<GROUP, 4>(a, L, Q, e8, e4, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw, bacc);
+    scan_segment<GROUP, 4>(a, L, Q, IC, e8, e4, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw,
+                             bacc);
     d = (d + (e4 - e8 + 7) / 8) % nwarps;
-    scan_segment<GROUP, 2>(a, L, Q, e4, e2, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw, bacc);
+    scan_segment<GROUP, 2>(a, L, Q, IC, e4, e2, (gw - d + nwarps) % nwarps, nwarps, tab, wb, sw,
+                             bacc);
     if (sw.nb > 0) flush_staged(Q, wb, sw.nb, bacc, lane);   // final flush
     if (sw.npairs) atomicAdd(&bacc.pairs[GROUP], sw.npairs);
     if (sw.ncands) atomicAdd(&bacc.candidates[GROUP], sw.ncands);
@@ -1842,6 +1883,12 @@ static int persistent_grid(pcc_ctx* ctx, const void* fn, int smem, int want_per_
 // Flags and contributions start at zero and are cleared by the finalize kernel.
 static size_t rec_off(size_t n) { return (10 * n + 3) & ~(size_t)3; }
 static size_t hist_off(size_t n) { return rec_off(n) + 8 * n; }
+// then, 16-byte aligned, the per-cell ion summaries (float4, see IonCache)
+static size_t ionsum_off(size_t n)
+{
+    const size_t nblk = (n + kClassBlock - 1) / kClassBlock;
+    return (hist_off(n) + 6 * kClasses + 8 + 3 * kClasses * nblk + 3) & ~(size_t)3;
+}
 
 static int ensure_lists(pcc_ctx* ctx, int n_cells)
 {
@@ -1849,8 +1896,7 @@ static int ensure_lists(pcc_ctx* ctx, int n_cells)
     if (ctx->lists) cudaFree(ctx->lists);
     ctx->lists = nullptr;
     ctx->lists_cells = 0;
-    const size_t nblk = ((size_t)n_cells + kClassBlock - 1) / kClassBlock;
-    const size_t bytes = (hist_off(n_cells) + 6 * kClasses + 8 + 3 * kClasses * nblk) * sizeof(int);
+    const size_t bytes = (ionsum_off(n_cells) + 4 * (size_t)n_cells) * sizeof(int);
     cudaError_t e = cudaMalloc(&ctx->lists, bytes);
     if (e == cudaSuccess) e = cudaMemset(ctx->lists, 0, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "pcc_collide: cell lists");
@@ -1894,6 +1940,15 @@ static CellList list_of(pcc_ctx* ctx, int group)
 
 static int* counters_of(pcc_ctx* ctx) { return ctx->lists + hist_off(ctx->lists_cells) + 6 * kClasses; }
 
+// counters: [0..2] cleared per group; [4] the call serial (never cleared)
+static IonCache ion_cache_of(pcc_ctx* ctx)
+{
+    IonCache C;
+    C.sum = reinterpret_cast<float4*>(ctx->lists + ionsum_off(ctx->lists_cells));
+    C.serial = reinterpret_cast<const unsigned*>(counters_of(ctx) + 4);
+    return C;
+}
+
 static Queue queue_of(pcc_ctx* ctx)
 {
     const size_t n = ctx->lists_cells;
@@ -1918,7 +1973,7 @@ template <int GROUP, int MINB>
 static void launch_scan(pcc_ctx* ctx, const StepArgs& a, const CellList& L, const Queue& Q, cudaStream_t st)
 {
     const int g = persistent_grid(ctx, (const void*)scan_kernel<GROUP, MINB>, 0, ctx->blocks_per_sm);
-    scan_kernel<GROUP, MINB><<<g, kBatchedThreads, 0, st>>>(a, L, Q);
+    scan_kernel<GROUP, MINB><<<g, kBatchedThreads, 0, st>>>(a, L, Q, ion_cache_of(ctx));
 }
 
 // Per group, after the class sort of all groups: counters, scan (register
@@ -1958,6 +2013,7 @@ static void launch_class_sort(pcc_ctx* ctx, const StepArgs& a, unsigned run, cud
     S.cnt_t = a.ion.count;
     S.n_cells = a.n_cells;
     S.run = run;
+    S.serial = reinterpret_cast<unsigned*>(counters_of(ctx) + 4);
     const int nblk = S.L[0].nblk;
     class_hist_kernel<<<nblk, kClassBlock, 0, st>>>(S);
     const size_t off_smem = (size_t)kClasses * nblk * sizeof(int);

@@ -199,32 +199,32 @@ def study(pcc, orc):
 
 
 def _write_table(st):
+    """Two markdown tables, one row per material state: the FP32 batched path
+    against the oracle, and the FP64 GPU path against the oracle."""
     wl, rec, tab = st["wl"], st["rec"], st["table"]
-    rows = []
+    f32, f64, o = rec["fp32"], rec["fp64"], rec["oracle"]
+    rows32, rows64 = [], []
     for m, mt in enumerate(wl.materials):
         LD, LTF = st["screening"][m][1], st["screening"][m][0]
-        f32, f64, o = rec["fp32"], rec["fp64"], rec["oracle"]
-        rows.append([
-            f"{'Ta' if mt.Z == 73 else 'Al'} {mt.Zstar:g}", f"{mt.T_e:g}", f"{LD / LTF:.3g}",
-            f"{st['pairs'][m]:.3g}", f"{st['events'][m]:.0f}", f"{tab[m, 0]:.1e} / {tab[m, 1]:.1e}",
-            f"{f32['mism'][m]:.0f} ({f32['mism'][m] / st['pairs'][m]:.1e})",
-            f"{f32['flips'][m]:.0f}", f"{f32['kerr'][m]:.1e}",
-            f"{f32['led_err'][m, 0]:.1e} / {f32['led_err'][m, 1]:.1e}",
+        name = f"{'Ta' if mt.Z == 73 else 'Al'} {mt.Zstar:g}"
+        rows32.append([
+            name, f"{mt.T_e:g}", f"{LD / LTF:.3g}", f"{st['pairs'][m]:.3g}", f"{st['events'][m]:.0f}",
+            f"{tab[m, 0]:.1e} / {tab[m, 1]:.1e}", f"{f32['mism'][m]:.0f} ({f32['mism'][m] / st['pairs'][m]:.1e})",
+            f"{f32['flips'][m]:.0f}", f"{f32['kerr'][m]:.1e}", f"{f32['led_err'][m, 0]:.1e} / {f32['led_err'][m, 1]:.1e}",
             f"{f32['m1'][m]:.1e} / {f32['m2'][m]:.1e}", f"{f32['ks_p'][m]:.2f}",
-            f"{f32['de'][:, m].max():.1e} / {f32['dq'][:, m].max():.1e}",
-            f"{f64['mism'][m]:.0f} / {f64['flips'][m]:.0f}", f"{f64['kerr'][m]:.1e}",
-            f"{f64['led_err'][m, 0]:.1e} / {f64['led_err'][m, 1]:.1e}",
-            f"{f64['m1'][m]:.1e} / {f64['m2'][m]:.1e}",
+            f"{f32['de'][:, m].max():.1e} / {f32['dq'][:, m].max():.1e}"])
+        rows64.append([
+            name, f"{mt.T_e:g}", f"{f64['mism'][m]:.0f} / {f64['flips'][m]:.0f}", f"{f64['kerr'][m]:.1e}",
+            f"{f64['led_err'][m, 0]:.1e} / {f64['led_err'][m, 1]:.1e}", f"{f64['m1'][m]:.1e} / {f64['m2'][m]:.1e}",
             f"{f64['de'][:, m].max():.1e} / {f64['dq'][:, m].max():.1e}",
-            f"{o['de'][:, m].max():.1e} / {o['dq'][:, m].max():.1e}",
-        ])
-    header = ["state (Z*)", "T_e eV", "L_D/L_TF", "pairs", "events", "FP32 table err Brems / BH",
-              "FP32 differing events (per pair)", "FP32 sampling flips", "FP32 photon k err",
-              "FP32 ledger err E / W", "FP32 <k> / <k^2> err", "FP32 KS p",
-              "FP32 drift E / q", "FP64 differing / flips", "FP64 photon k err", "FP64 ledger err E / W",
-              "FP64 <k> / <k^2> err",
-              "FP64 drift E / q", "oracle drift E / q"]
-    text = PS.markdown_table(header, rows)
+            f"{o['de'][:, m].max():.1e} / {o['dq'][:, m].max():.1e}"])
+    h32 = ["state (Z*)", "T_e (eV)", "L_D/L_TF", "pairs", "events", "σ table err Brems / BH",
+           "differing events (per pair)", "sampling flips", "photon k err", "ledger err E / W",
+           "⟨k⟩ / ⟨k²⟩ err", "KS p", "drift per step E / q"]
+    h64 = ["state (Z*)", "T_e (eV)", "differing events / flips", "photon k err", "ledger err E / W",
+           "⟨k⟩ / ⟨k²⟩ err", "drift per step E / q", "oracle drift per step E / q"]
+    text = ("FP32 batched path against the FP64 oracle\n\n" + PS.markdown_table(h32, rows32)
+            + "\n\nFP64 GPU path against the FP64 oracle\n\n" + PS.markdown_table(h64, rows64))
     for lab in ("fp32", "fp64"):
         ka = np.concatenate(rec[lab]["kerr_all"])
         q = np.quantile(ka, [0.5, 0.99, 0.9999, 1.0])
