@@ -549,35 +549,85 @@ def config2_measure(ctx, pcc, torch, W, steps=100, plain_steps=3):
     return res
 
 
+# Slack of the end-to-end layout: each step starts again from the host state,
+# so a region needs room for one step's secondaries only (about 4e4 events
+# per step over 2^20 cells: a few in a small cell, 2 % covers the largest).
+E2E_SLACK = {"em": (4, 0.02), "ep": (4, 0.0), "ph": (4, 0.02)}
+
+
+def h2d_rate(torch, nbytes=1 << 30, reps=3):
+    """Pinned host-to-device copy rate of this machine, GB/s (best of reps)."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    best = 0.0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d.copy_(h, non_blocking=True)
+        torch.cuda.synchronize()
+        best = max(best, nbytes / (time.perf_counter() - t0) / 1e9)
+    del h, d
+    return best
+
+
+def live_records(torch, sp):
+    """The live particles of a species in storage order, as pcc_bin input."""
+    cnt = sp.cell_count.long()
+    n_cells = cnt.numel()
+    n = int(cnt.sum())
+    cell = torch.repeat_interleave(torch.arange(n_cells, device=cnt.device, dtype=torch.int32), cnt)
+    first = torch.repeat_interleave(sp.cell_start[:-1].long(), cnt)
+    run0 = torch.cumsum(cnt, 0) - cnt
+    idx = first + (torch.arange(n, device=cnt.device) - torch.repeat_interleave(run0, cnt))
+    return {"ux": sp.ux[idx], "uy": sp.uy[idx], "uz": sp.uz[idx], "w": sp.w[idx], "pid": sp.pid[idx], "cell": cell,
+            "x": None, "n": n}
+
+
 def e2e_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, seed, prec):
-    """Same step through the C ABI, with every step's particle state copied in
-    from pinned host buffers and the step's counters and ledger read back."""
+    """Same step through the C ABI, with every step's particle state copied
+    in from pinned host buffers and the step's counters and ledger read back.
+    The state is held in a layout of its own whose regions keep only the slack
+    one step needs, so the copies are the live records plus about 3 %: per
+    species the momenta, weights and ids of every slot and the live count of
+    every cell (the ions, which a step only reads, stay resident)."""
     names = ("em", "ep", "ph")
-    fields = ("ux", "uy", "uz", "w", "pid")
-    host = {k: {f: getattr(dev[k], f).cpu().pin_memory() for f in fields} for k in names}
+    fields = ("ux", "uy", "uz", "w", "pid", "cell_count")
+    state = {}
+    for k in names:
+        live = live_records(torch, dev[k])
+        sa, sr = E2E_SLACK[k]
+        cap = int(live["n"] + sa * n_cells + int(np.ceil(sr * live["n"])) + n_cells)
+        sp = pcc.DeviceSpecies.empty(n_cells, cap)
+        empty = {"n": 0, "ux": None, "uy": None, "uz": None, "w": None, "pid": None, "cell": None}
+        pcc.bin(ctx, live if live["n"] else empty, n_cells, sp, slack_abs=sa, slack_rel=sr)
+        state[k] = sp
+        del live
+    host = {k: {f: getattr(state[k], f).cpu().pin_memory() for f in fields} for k in names}
     ledger = torch.zeros((n_cells, 4), dtype=torch.float32, device="cuda")
     led_h = torch.zeros((n_cells, 4), dtype=torch.float32).pin_memory()
     h2d = sum(t.numel() * t.element_size() for d in host.values() for t in d.values())
     d2h = led_h.numel() * 4 + 13 * 8
-    stream = torch.cuda.current_stream()
+    live_bytes = 24 * sum(int(state[k].cell_count.sum()) for k in names)
     n = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in range(n):
         for k in names:
             for f in fields:
-                getattr(dev[k], f).copy_(host[k][f], non_blocking=True)
-        pcc.collide(ctx, n_cells, mat_of_cell, ion_mass, dev["em"], dev["ep"], dev["ph"], dev["ion"], dt, seed,
+                getattr(state[k], f).copy_(host[k][f], non_blocking=True)
+        pcc.collide(ctx, n_cells, mat_of_cell, ion_mass, state["em"], state["ep"], state["ph"], dev["ion"], dt, seed,
                     10_000 + s, precision=prec, ledger=ledger)
         for k in names:
-            pcc.append_secondaries(ctx, n_cells, dev[k])
+            pcc.append_secondaries(ctx, n_cells, state[k])
         led_h.copy_(ledger, non_blocking=True)
-        _, st = ctx.read_status(stream)
+        status, st = ctx.read_status(torch.cuda.current_stream())
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     pairs = sum(st["pairs"])
+    del state, host
     return {"value": pairs / (el / n), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "steps": n}
+            "live_record_bytes_per_step": int(live_bytes), "steps": n, "status": status,
+            "ms_per_step": 1e3 * el / n, "h2d_gbs_measured": h2d_rate(torch)}
 
 
 # ---------------------------------------------------------- CPU oracle leg --

@@ -90,3 +90,20 @@ def test_cpu_baseline_states_its_cores(monkeypatch):
     assert out["value_1t"] > 0 and out["value_omp"] > 0 and out["value"] == out["value_omp"]
     assert 1 <= out["cores"] <= out["cores_available"] and out["kind"] == "oracle"
     assert "fixed subset" in out["sample"]
+
+
+def test_live_records_gather_the_live_slots():
+    """The end-to-end leg's gather of a cell-region layout: every cell's live
+    slots in storage order, with their cell index, and nothing of the slack."""
+    import types
+    torch = pytest.importorskip("torch")
+    start = torch.tensor([0, 3, 3, 7], dtype=torch.int32)
+    count = torch.tensor([2, 0, 3], dtype=torch.int32)
+    vals = torch.arange(7, dtype=torch.float32) * 10
+    sp = types.SimpleNamespace(cell_start=start, cell_count=count, ux=vals, uy=vals + 1, uz=vals + 2, w=vals + 3,
+                               pid=torch.arange(7, dtype=torch.int64) + 100)
+    d = bench.live_records(torch, sp)
+    assert d["n"] == 5
+    assert d["ux"].tolist() == [0.0, 10.0, 30.0, 40.0, 50.0]
+    assert d["pid"].tolist() == [100, 101, 103, 104, 105]
+    assert d["cell"].tolist() == [0, 0, 2, 2, 2]
