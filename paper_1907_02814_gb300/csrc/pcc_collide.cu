@@ -1274,8 +1274,9 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
     const uint32_t step32 = (uint32_t)a.step;
     const int ntup = (e1 - e0 + C - 1) / C;
     const int e_lane = e0 + gi;   // entry of tuple t for this lane: e_lane + t C
-    // Two-stage prefetch: the metadata of the tuple after next, and the first
-    // G weights of both lists of the next tuple, load while a tuple is scanned.
+    // Two-stage prefetch: the metadata of the tuple after next, and (electron
+    // scan) the first G ion weights of the next tuple, load while a tuple is
+    // scanned.
     constexpr bool kWriter = GROUP == kGroupEm;   // the electron scan writes the ion summaries
     const auto first_ion = [&](const CellMeta& m) -> float {
         return (uint32_t)gl < m.Nt ? I.w[m.t0 + gl] : 0.f;
@@ -1287,19 +1288,16 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
     CellMeta next = load_meta(a, P, t < ntup && e_lane + t * C < e1 ? L.list[e_lane + t * C] : -1);
     float next_tw = kWriter ? first_ion(next) : 0.f;
     float4 next_is = kWriter ? make_float4(0.f, 0.f, 0.f, 0.f) : ion_sum(next);
-    float next_pw = (uint32_t)gl < next.Np ? P.w[next.p0 + gl] : 0.f;
     int t2 = t + nwarps;
     CellMeta next2 = load_meta(a, P, t2 < ntup && e_lane + t2 * C < e1 ? L.list[e_lane + t2 * C] : -1);
     while (t < ntup) {
         const CellMeta cm = next;
         float tw0 = next_tw;
-        const float pw0 = next_pw;   // weights of slot gl of this cell
         const float4 is = next_is;   // its ion summary (readers)
         t += nwarps;
         next = next2;
         if constexpr (kWriter) next_tw = first_ion(next);
         else next_is = ion_sum(next);
-        next_pw = (uint32_t)gl < next.Np ? P.w[next.p0 + gl] : 0.f;
         t2 = t + nwarps;
         next2 = load_meta(a, P, t2 < ntup && e_lane + t2 * C < e1 ? L.list[e_lane + t2 * C] : -1);
         uint32_t Np = cm.Np, Nt = cm.Nt;
@@ -1330,6 +1328,10 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
         float sp = 0.f, st = 0.f, sf = 0.f, b2 = 0.f;
         bool uni = have ? is.z > 0.f : true;
         if (!have) {
+            // beta^2 = u^2 / (1 + u^2) is increasing in u^2: the lane keeps
+            // the largest u^2, and the sum of them only to see whether any
+            // was non-finite (then beta = 1)
+            float u2m = 0.f, u2s = 0.f;
 #pragma unroll 4
             for (uint32_t s = gl; s < Nt; s += G) {
                 const float wt = s < (uint32_t)G ? tw0 : I.w[t0 + s];
@@ -1338,11 +1340,12 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
                 if constexpr (kWriter) {
                     const float ux = I.ux[t0 + s], uy = I.uy[t0 + s], uz = I.uz[t0 + s];
                     const float u2 = ux * ux + uy * uy + uz * uz;
-                    b2 = fmaxf(b2, isfinite(u2) ? __fdividef(u2, 1.f + u2) : 1.f);
-                } else {
-                    b2 = 1.f;
+                    u2m = fmaxf(u2m, u2);
+                    u2s += u2;
                 }
             }
+            if constexpr (kWriter) b2 = isfinite(u2s) ? u2m / (1.f + u2m) : 1.f;
+            else b2 = (uint32_t)gl < Nt ? 1.f : 0.f;
         }
         const float st_sum = group_sum<G>(st);
         const float n_t = have ? is.x : st_sum;
@@ -1355,15 +1358,26 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
                 IC.sum[cell] = make_float4(n_t, w0, uni ? bfac : -bfac, __uint_as_float(*IC.serial));
         }
         if (caseA) {
-#pragma unroll 4
-            for (uint32_t s = gl; s < Np; s += G) {
-                const float wp = s < (uint32_t)G ? pw0 : P.w[p0 + s];
+            // the weights as float4 from the region's first 16-byte boundary
+            // (its start rounded up), the ragged head and tail (at most 3 + 3
+            // weights) one by one
+            const uint32_t al = (uint32_t)((reinterpret_cast<uintptr_t>(P.w + p0) >> 2) & 3u);
+            const uint32_t hd = min((4u - al) & 3u, Np), nb = (Np - hd) >> 2, tl = Np - hd - 4 * nb;
+            const float4* W4 = reinterpret_cast<const float4*>(P.w + p0 + hd);
+#pragma unroll 2
+            for (uint32_t v = gl; v < nb; v += G) {
+                const float4 q = W4[v];
+                sp += (q.x + q.y) + (q.z + q.w);
+                sf += (fminf(q.x, w0) + fminf(q.y, w0)) + (fminf(q.z, w0) + fminf(q.w, w0));
+            }
+            for (uint32_t i = gl; i < hd + tl; i += G) {
+                const float wp = P.w[p0 + (i < hd ? i : 4 * nb + i)];
                 sp += wp;
                 sf += fminf(wp, w0);
             }
         } else {   // projectile s takes part in ceil((N_t - s) / N_p) pairs
             for (uint32_t s = gl; s < Np; s += G) {
-                const float wp = s < (uint32_t)G ? pw0 : P.w[p0 + s];
+                const float wp = P.w[p0 + s];
                 sp += wp;
                 sf += fminf(wp, w0) * (float)((Nt - s + Np - 1) / Np);
             }
