@@ -1177,6 +1177,40 @@ __device__ __forceinline__ bool bh_candidate(const StepArgs& a, const Tab<float>
 
 constexpr int kWarpBuf = 128;   // per-warp staging of candidates before the flat queue
 
+// Philox4x32-10 on counters (x, c1, c2, c3) with only x varying: the first
+// round's product of c2 and the second round's product of the first word do
+// not depend on x, so they are taken once (PhiloxFixed) and each draw
+// multiplies 18 times instead of 20.  The result equals draw_k(x, c1, c2, c3).
+struct PhiloxFixed { uint32_t t0, b1, c1k, d1; };
+__device__ __forceinline__ PhiloxFixed philox_fixed(uint32_t c1, uint32_t c2, uint32_t c3, const PhiloxKeys& K)
+{
+    const uint64_t m1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t a = (uint32_t)(m1 >> 32) ^ c1 ^ K.k0[0];   // word 0 after round 1
+    const uint64_t m0 = (uint64_t)0xD2511F53u * a;             // its round-2 product
+    PhiloxFixed f;
+    f.t0 = c3 ^ K.k1[0];
+    f.b1 = (uint32_t)m1 ^ K.k0[1];
+    f.c1k = (uint32_t)(m0 >> 32) ^ K.k1[1];
+    f.d1 = (uint32_t)m0;
+    return f;
+}
+__device__ __forceinline__ Philox4 draw_fixed(uint32_t x, const PhiloxFixed& f, const PhiloxKeys& K)
+{
+    const uint64_t p0 = (uint64_t)0xD2511F53u * x;                 // round 1
+    const uint32_t w2 = (uint32_t)(p0 >> 32) ^ f.t0, w3 = (uint32_t)p0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * w2;                // round 2
+    uint32_t c0 = (uint32_t)(p1 >> 32) ^ f.b1, c1 = (uint32_t)p1, c2 = f.c1k ^ w3, c3 = f.d1;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const uint64_t m0 = (uint64_t)0xD2511F53u * c0, m1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ K.k0[r], n2 = (uint32_t)(m0 >> 32) ^ c3 ^ K.k1[r];
+        c1 = (uint32_t)m1; c3 = (uint32_t)m0; c0 = n0; c2 = n2;
+    }
+    Philox4 o;
+    o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+    return o;
+}
+
 // Sum over the G consecutive lanes of an aligned lane group (G a power of two).
 template <int G, typename T>
 __device__ __forceinline__ T group_sum(T v)
@@ -1409,15 +1443,16 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
         // ---- cells with N_p >= N_t: one pair per projectile slot
         const uint32_t itA = active && caseA ? (Np + 2 * G - 1) / (2 * G) : 0u;
         const uint32_t nitA = G == 32 ? itA : __reduce_max_sync(kFull, itA);
-        const uint32_t tag0 = stream_tag(GROUP, kAccept, 0);
+        const PhiloxFixed pf = philox_fixed((uint32_t)cell, step32, stream_tag(GROUP, kAccept, 0), a.keys);
         uint32_t mine = 0;   // candidates of this lane
         for (uint32_t it = 0; it < nitA; ++it) {
             const uint32_t base = it * (2 * G);
-            const Philox4 ph = draw_k((base >> 1) + gl, (uint32_t)cell, step32, tag0, a.keys);
+            const Philox4 ph = draw_fixed((base >> 1) + gl, pf, a.keys);
             const bool live = G == 32 || it < itA;
             const uint32_t s0 = base + 2 * gl;
-            const bool c0 = live && s0 < Np && (ph.v[0] <= k1 || ph.v[1] <= k2);
-            const bool c1 = live && s0 + 1 < Np && (ph.v[2] <= k1 || ph.v[3] <= k2);
+            // (the photon group has one accept word per pair)
+            const bool c0 = live && s0 < Np && (ph.v[0] <= k1 || (GROUP != kGroupPh && ph.v[1] <= k2));
+            const bool c1 = live && s0 + 1 < Np && (ph.v[2] <= k1 || (GROUP != kGroupPh && ph.v[3] <= k2));
             // most iterations of small cells have no candidate in the warp
             if (__any_sync(kFull, c0 || c1)) {
                 const unsigned m0 = __ballot_sync(kFull, c0);
@@ -1451,7 +1486,7 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
             for (int h = 0; h < 2; ++h) {
                 const uint32_t s = 2 * q + h, j = s + mp * Np;
                 const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
-                const bool cand = valid && s < Np && j < Nt && (r1 <= k1 || r2 <= k2);
+                const bool cand = valid && s < Np && j < Nt && (r1 <= k1 || (GROUP != kGroupPh && r2 <= k2));
                 const unsigned m = __ballot_sync(kFull, cand);
                 if (cand) Q.qb[t0 + cnt + __popc(m & gmask & below)] = j;
                 cnt += __popc(m & gmask);
