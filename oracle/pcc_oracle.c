@@ -1012,12 +1012,14 @@ static void pair_of(uint32_t j, uint32_t Np, uint32_t Nt, const uint32_t rk[4], 
  * species but are not projectiles until the next step; ions are never
  * modified.  Random numbers: Philox4x32-10, key = seed, counter
  *   permutation keys:  (0,      cell, step, group | PERM<<4)
- *   accept word r:     (s>>1,   cell, step, group | ACCEPT<<4 | m<<8),
- *                      words 2(s&1) (Brems or BH) and 2(s&1)+1 (Trident),
- *                      s = projectile slot in id order, m = pass index;
+ *   accept word r:     e+-: (s>>1, cell, step, group | ACCEPT<<4 | m<<8),
+ *                      words 2(s&1) (Brems) and 2(s&1)+1 (Trident);
+ *                      photons (one word per pair, BH): (s>>2, ...),
+ *                      word s&3; s = projectile slot in id order,
+ *                      m = pass index;
  *                      its second word r' (only when r = floor(2^32 p)):
- *                      the same word of (s>>1, cell, step,
- *                      group | ACCEPT_EXT<<4 | m<<8), see accept_u
+ *                      the same word of the same counter with
+ *                      ACCEPT_EXT in place of ACCEPT, see accept_u
  *   event draws:       (j,      cell, step, group | EVT<<4)
  * with U = ((r >> 9) + 1/2) 2^-23 for the event draws.
  */
@@ -1113,20 +1115,24 @@ int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
                 uint32_t s, tau;
                 pair_of(j, Np, Nt, rk, &s, &tau);
                 uint32_t m = Np >= Nt ? 0 : j / Np;
+                /* e+-: two accept words per pair, two pairs per draw;
+                 * photons: one word per pair, four pairs per draw */
+                uint32_t ctr = g < 2 ? s >> 1 : s >> 2;
+                int wd = g < 2 ? (int)(2 * (s & 1)) : (int)(s & 3);
                 uint32_t acc[4];
-                philox_at(s >> 1, (uint32_t)cell, step, tag(g, PU_ACCEPT, m), seed, acc);
-                accept_src s1 = { s >> 1, (uint32_t)cell, step, tag(g, PU_ACCEPT_EXT, m), seed, (int)(2 * (s & 1)) };
+                philox_at(ctr, (uint32_t)cell, step, tag(g, PU_ACCEPT, m), seed, acc);
+                accept_src s1 = { ctr, (uint32_t)cell, step, tag(g, PU_ACCEPT_EXT, m), seed, wd };
                 accept_src s2 = s1;
                 s2.w += 1;
                 int ip = pidx[s], it = tidx[tau];
                 if (g < 2) {
                     if (mask & ORC_PROC_BREMS)
-                        cerr |= brems_pair(&c, g, P, ip, ion, it, j, acc[2 * (s & 1)], &s1, ph);
+                        cerr |= brems_pair(&c, g, P, ip, ion, it, j, acc[wd], &s1, ph);
                     if (mask & ORC_PROC_TRIDENT)
-                        cerr |= trident_pair(&c, g, P, ip, ion, it, j, acc[2 * (s & 1) + 1], &s2, em, ep);
+                        cerr |= trident_pair(&c, g, P, ip, ion, it, j, acc[wd + 1], &s2, em, ep);
                 } else {
                     if (dead[ip]) continue;
-                    if (bh_pair(&c, P, ip, ion, it, j, acc[2 * (s & 1)], &s1, em, ep, &cerr)) dead[ip] = 1;
+                    if (bh_pair(&c, P, ip, ion, it, j, acc[wd], &s1, em, ep, &cerr)) dead[ip] = 1;
                 }
             }
             if (cerr) {

@@ -638,12 +638,13 @@ __device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
     const bool has_x = P.x != nullptr;
     const bool quick = sizeof(Real) == 4;
     const uint32_t kBH = quick ? accept_threshold((float)(coef * (Real)a.f_bound[3 * mat + 2])) : 0u;
-    for (uint32_t q = grp.rank(); 2 * q < Np; q += grp.size()) {
-        const int nh = (2 * q + 1 < Np) ? 2 : 1;
+    // one accept word per pair (BH): slots 4q .. 4q + 3 share the draw of counter q
+    for (uint32_t q = grp.rank(); 4 * q < Np; q += grp.size()) {
+        const int nh = Np - 4 * q < 4u ? (int)(Np - 4 * q) : 4;
         Philox4 ac{};
         if (pr.caseA) ac = draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, 0), a.seed);
         for (int h = 0; h < nh; ++h) {
-            const uint32_t s = 2 * q + h;
+            const uint32_t s = 4 * q + h;
             const int sl = p0 + (int)s;
             const uint32_t npass = pr.caseA ? 1u : (Nt - s + Np - 1) / Np;
             bool loaded = false;
@@ -651,7 +652,7 @@ __device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
             for (uint32_t m = 0; m < npass; ++m) {
                 uint32_t j, tau;
                 const uint32_t rw =
-                    pr.caseA ? ac.v[2 * h] : draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed).v[2 * h];
+                    pr.caseA ? ac.v[h] : draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed).v[h];
                 if (quick && !(rw <= kBH)) continue;   // exact quick reject
                 if (pr.caseA) {
                     j = pr.pair_of_slot(s);
@@ -677,7 +678,7 @@ __device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
                 if (!(sig > (Real)0)) continue;
                 const Real x = coef * sig * kp / (k * f.gi);
                 if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
-                const AcceptSrc src{q, (uint32_t)cell, stream_tag(kGroupPh, kAcceptExt, m), 2 * h};
+                const AcceptSrc src{q, (uint32_t)cell, stream_tag(kGroupPh, kAcceptExt, m), h};
                 if (!accept_u<Real>(rw, -expm1(-x), src, a.step, a.seed)) continue;
                 acc.accepted[kChBH]++;
                 const Real fac = d / (f.gi + (Real)1) - k;
@@ -1175,7 +1176,22 @@ __device__ __forceinline__ bool bh_candidate(const StepArgs& a, const Tab<float>
     return true;
 }
 
-constexpr int kWarpBuf = 128;   // per-warp staging of candidates before the flat queue
+constexpr int kWarpBuf = 256;   // per-warp staging of candidates before the flat queue
+
+// The accept words of projectile slot s (random-stream layout): an e+- pair
+// takes words 2(s&1) (Brems) and 2(s&1)+1 (Trident) of counter s>>1; a photon
+// pair, which has one accept word (BH), word s&3 of counter s>>2.
+template <int GROUP>
+struct AcceptSlots {
+    static constexpr uint32_t kPerDraw = GROUP == kGroupPh ? 4u : 2u;
+    static __device__ __forceinline__ uint32_t ctr(uint32_t s) { return GROUP == kGroupPh ? s >> 2 : s >> 1; }
+    static __device__ __forceinline__ uint32_t word(uint32_t s) { return GROUP == kGroupPh ? (s & 3u) : 2u * (s & 1u); }
+    // slot kPerDraw q + h of a draw: may the pair be accepted under thresholds k1 (Brems or BH), k2 (Trident)?
+    static __device__ __forceinline__ bool hit(const Philox4& d, int h, uint32_t k1, uint32_t k2)
+    {
+        return GROUP == kGroupPh ? d.v[h] <= k1 : (d.v[2 * h] <= k1 || d.v[2 * h + 1] <= k2);
+    }
+};
 
 // Philox4x32-10 on counters (x, c1, c2, c3) with only x varying: the first
 // round's product of c2 and the second round's product of the first word do
@@ -1440,40 +1456,46 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
         uint32_t k1 = 0, k2 = 0;
         if (active) bound_thresholds<GROUP>(a, mat, coef * (0.5f * bfac), k1, k2);
         uint32_t ncand = 0;   // candidates of this lane's cell (uniform over its group)
-        // ---- cells with N_p >= N_t: one pair per projectile slot
-        const uint32_t itA = active && caseA ? (Np + 2 * G - 1) / (2 * G) : 0u;
+        // ---- cells with N_p >= N_t: one pair per projectile slot; a lane
+        // takes the S slots of one draw per iteration (S = 2 for e+-, 4 for
+        // photons)
+        using AS = AcceptSlots<GROUP>;
+        constexpr uint32_t S = AS::kPerDraw;
+        const uint32_t itA = active && caseA ? (Np + S * G - 1) / (S * G) : 0u;
         const uint32_t nitA = G == 32 ? itA : __reduce_max_sync(kFull, itA);
         const PhiloxFixed pf = philox_fixed((uint32_t)cell, step32, stream_tag(GROUP, kAccept, 0), a.keys);
         uint32_t mine = 0;   // candidates of this lane
         for (uint32_t it = 0; it < nitA; ++it) {
-            const uint32_t base = it * (2 * G);
-            const Philox4 ph = draw_fixed((base >> 1) + gl, pf, a.keys);
+            const Philox4 ph = draw_fixed(it * G + gl, pf, a.keys);
             const bool live = G == 32 || it < itA;
-            const uint32_t s0 = base + 2 * gl;
-            // (the photon group has one accept word per pair)
-            const bool c0 = live && s0 < Np && (ph.v[0] <= k1 || (GROUP != kGroupPh && ph.v[1] <= k2));
-            const bool c1 = live && s0 + 1 < Np && (ph.v[2] <= k1 || (GROUP != kGroupPh && ph.v[3] <= k2));
+            const uint32_t s0 = (it * G + gl) * S;
+            bool c[S], anyc = false;
+#pragma unroll
+            for (int h = 0; h < (int)S; ++h) {
+                c[h] = live && s0 + h < Np && AS::hit(ph, h, k1, k2);
+                anyc |= c[h];
+            }
             // most iterations of small cells have no candidate in the warp
-            if (__any_sync(kFull, c0 || c1)) {
-                const unsigned m0 = __ballot_sync(kFull, c0);
-                if (c0) wb[sw.nb + __popc(m0 & below)] = make_uint2((uint32_t)cell, s0);
-                sw.nb += __popc(m0);
-                const unsigned m1 = __ballot_sync(kFull, c1);
-                if (c1) wb[sw.nb + __popc(m1 & below)] = make_uint2((uint32_t)cell, s0 + 1);
-                sw.nb += __popc(m1);
-                mine += (uint32_t)c0 + (uint32_t)c1;
-                if (sw.nb > kWarpBuf - 64) {   // flush the staging buffer to the flat queue
+            if (__any_sync(kFull, anyc)) {
+#pragma unroll
+                for (int h = 0; h < (int)S; ++h) {
+                    const unsigned m = __ballot_sync(kFull, c[h]);
+                    if (c[h]) wb[sw.nb + __popc(m & below)] = make_uint2((uint32_t)cell, s0 + h);
+                    sw.nb += __popc(m);
+                    mine += (uint32_t)c[h];
+                }
+                if (sw.nb > kWarpBuf - 32 * (int)S) {   // flush before the next iteration could overfill it
                     flush_staged(Q, wb, sw.nb, bacc, lane);
                     sw.nb = 0;
                 }
             }
         }
         ncand = group_sum<G>(mine);
-        // ---- cells with N_p < N_t.  Draw units (pass m, slot pair q): unit
-        // i = m Qn + q covers slots 2q and 2q+1 of pass m, i.e. pairs
+        // ---- cells with N_p < N_t.  Draw units (pass m, draw q): unit
+        // i = m Qn + q covers slots S q .. S q + S - 1 of pass m, i.e. pairs
         // j = s + m N_p.  A group's lanes take consecutive units, so each
         // projectile's pairs are queued in increasing j.
-        const uint32_t Qn = (Np + 1) >> 1, passes = Np ? (Nt + Np - 1) / Np : 0u, units = Qn * passes;
+        const uint32_t Qn = (Np + S - 1) / S, passes = Np ? (Nt + Np - 1) / Np : 0u, units = Qn * passes;
         const uint32_t itB = active && !caseA ? (units + G - 1) / G : 0u;
         const uint32_t nitB = G == 32 ? itB : __reduce_max_sync(kFull, itB);
         uint32_t cnt = 0;
@@ -1483,10 +1505,9 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
             const uint32_t mp = valid ? i / Qn : 0u, q = valid ? i - mp * Qn : 0u;
             const Philox4 ph = draw_k(q, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t s = 2 * q + h, j = s + mp * Np;
-                const uint32_t r1 = ph.v[2 * h], r2 = ph.v[2 * h + 1];
-                const bool cand = valid && s < Np && j < Nt && (r1 <= k1 || (GROUP != kGroupPh && r2 <= k2));
+            for (int h = 0; h < (int)S; ++h) {
+                const uint32_t s = S * q + h, j = s + mp * Np;
+                const bool cand = valid && s < Np && j < Nt && AS::hit(ph, h, k1, k2);
                 const unsigned m = __ballot_sync(kFull, cand);
                 if (cand) Q.qb[t0 + cnt + __popc(m & gmask & below)] = j;
                 cnt += __popc(m & gmask);
@@ -1628,9 +1649,11 @@ __global__ void __launch_bounds__(kBatchedThreads, 4) flat_cand_kernel(const __g
         rk.k[0] = kp.v[0]; rk.k[1] = kp.v[1]; rk.k[2] = kp.v[2]; rk.k[3] = kp.v[3];
         const uint32_t j = Np <= 32 ? perm_pos_small(s, Np, rk) : perm_pos_large(s, Np, rk);
         const int ts = cm.t0 + (int)fast_mod(j, Nt, 1.0f / (float)Nt);
-        const Philox4 ph = draw_k(s >> 1, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, 0), a.keys);
-        const uint32_t r1 = ph.v[2 * (s & 1u)], r2 = ph.v[2 * (s & 1u) + 1];
-        const AcceptSrc src{s >> 1, (uint32_t)cell, stream_tag(GROUP, kAcceptExt, 0), (int)(2 * (s & 1u))};
+        using AS = AcceptSlots<GROUP>;
+        const uint32_t wd = AS::word(s);
+        const Philox4 ph = draw_k(AS::ctr(s), (uint32_t)cell, step32, stream_tag(GROUP, kAccept, 0), a.keys);
+        const uint32_t r1 = ph.v[wd], r2 = GROUP == kGroupPh ? 0u : ph.v[wd + 1];
+        const AcceptSrc src{AS::ctr(s), (uint32_t)cell, stream_tag(GROUP, kAcceptExt, 0), (int)wd};
         const int sl = cm.p0 + (int)s;
         float rad = 0.f, wcre = 0.f;
         bool event = false;
@@ -1700,9 +1723,11 @@ __global__ void __launch_bounds__(kBatchedThreads, 2) caseb_cand_kernel(const __
             for (int k = 0; k < cnt; ++k) {
                 const uint32_t j = Q.qb[cm.t0 + k];
                 const uint32_t s = j % Np, mp = j / Np;
-                const Philox4 ph = draw_k(s >> 1, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
-                const uint32_t r1 = ph.v[2 * (s & 1u)], r2 = ph.v[2 * (s & 1u) + 1];
-                const AcceptSrc src{s >> 1, (uint32_t)cell, stream_tag(GROUP, kAcceptExt, mp), (int)(2 * (s & 1u))};
+                using AS = AcceptSlots<GROUP>;
+                const uint32_t wd = AS::word(s);
+                const Philox4 ph = draw_k(AS::ctr(s), (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
+                const uint32_t r1 = ph.v[wd], r2 = GROUP == kGroupPh ? 0u : ph.v[wd + 1];
+                const AcceptSrc src{AS::ctr(s), (uint32_t)cell, stream_tag(GROUP, kAcceptExt, mp), (int)wd};
                 const uint32_t t = Nt <= 32 ? (uint32_t)tab[j] : perm_elem_large(j, Nt, rk);
                 const int ts = cm.t0 + (int)t, sl = cm.p0 + (int)s;
                 bool event = false;
