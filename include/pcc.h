@@ -139,7 +139,7 @@ typedef struct {
     unsigned long long created[5];   /* events kept by the weight correction          */
     double energy_change;            /* sum over events of W (E_out - E_in), m_e c^2 m^-3 */
     double charge_change;            /* sum over events of W (q_out - q_in), e m^-3        */
-    unsigned long long candidates[3];/* batched path: pairs whose accept word fell below
+    unsigned long long candidates[3];/* batched path: pairs whose accept digit fell below
                                         the per-material bound, evaluated in full        */
 } pcc_stats;
 
@@ -204,13 +204,13 @@ int pcc_bin(pcc_ctx *ctx, const pcc_particles *in, int n_cells, pcc_species *out
  * from Brems, e-/e+ from Trident and BH); absorbed photons removed.  ion may
  * not be NULL; em, ep, ph may have zero live particles but not be NULL.
  * A pair collides if U < p, p = 1 - exp(-x), for the uniform
- * U = (2^32 r + r' + 1/2) 2^-64 compared digit by digit: the pair's accept
- * word r settles it unless r = floor(2^32 p), and only then is the second
- * word r' drawn, so even per-pair probabilities far below 1e-7 (small time
- * steps, rare processes) are honoured (see pcc_accept_check).
+ * U = (2^48 a + e + 1/2) 2^-64 compared digit by digit: the pair's 16-bit
+ * accept digit a settles it unless a = floor(2^16 p), and only then is the
+ * 48-bit rest e drawn, so even per-pair probabilities far below 1e-7 (small
+ * time steps, rare processes) are honoured (see pcc_accept_check).
  * precision PCC_FP64_PLAIN: one thread block per cell, FP64 arithmetic;
  * PCC_FP32_BATCHED: persistent kernel, FP32 arithmetic, and a pair whose
- * accept word exceeds floor(2^32 b) for a per-material bound b of its
+ * accept digit exceeds floor(2^16 b) for a per-material bound b of its
  * acceptance probability is rejected without being evaluated (exact, since
  * 1 - exp(-x) <= x <= b; the Trident bound assumes ion-frame Lorentz factors
  * below 1e7).  ledger: optional device float[n_cells][4], per cell {radiated
@@ -265,17 +265,18 @@ int pcc_set_wait_limit(pcc_ctx *ctx, int polls);
 int pcc_append_secondaries(pcc_ctx *ctx, int n_cells, pcc_species *sp, void *stream);
 
 /* Diagnostic: the accept decision of the collision kernels (Eq. proba3: a
- * pair collides if U < p, p = 1 - exp(-x)) for n given accept words r[i] and
- * probabilities p[i].  U = (2^32 r + r' + 1/2) 2^-64 is compared with p
- * digit by digit: r settles it unless r = floor(2^32 p); only then is r'
- * drawn, as word w[i] of the Philox4x32-10 draw with counter
- * (c0[i], cell[i], step, tag[i]) and key seed.  out64[i]: the decision with
- * p in FP64 (the plain path); out32[i]: with p rounded to FP32 (the batched
- * path).  Device arrays of n entries (outputs 0 or 1).  PCC_E_INVALID for
- * n < 0 or a null array.  Asynchronous. */
+ * pair collides if U < p, p = 1 - exp(-x)) for n given 16-bit accept digits
+ * r[i] (in [0, 2^16); a larger value is never accepted unless p >= 1) and
+ * probabilities p[i].  U = (2^48 r + e + 1/2) 2^-64 is compared with p
+ * digit by digit: r settles it unless r = floor(2^16 p); only then is the
+ * 48-bit rest e = 2^16 w0 + (w1 >> 16) drawn, from words w0, w1 of the
+ * Philox4x32-10 draw with counter (c0[i], cell[i], step, tag[i]) and key
+ * seed.  out64[i]: the decision with p in FP64 (the plain path); out32[i]:
+ * with p rounded to FP32 (the batched path).  Device arrays of n entries
+ * (outputs 0 or 1).  PCC_E_INVALID for n < 0 or a null array.
+ * Asynchronous. */
 int pcc_accept_check(int n, const uint32_t *r, const double *p, const uint32_t *c0, const uint32_t *cell,
-                     const uint32_t *tag, const int *w, uint64_t step, uint64_t seed, int *out32, int *out64,
-                     void *stream);
+                     const uint32_t *tag, uint64_t step, uint64_t seed, int *out32, int *out64, void *stream);
 
 /* Diagnostic: the pairing of Sec. III.A for one projectile species against
  * the targets.  For live projectile slot s of cell c (written at index

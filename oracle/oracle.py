@@ -104,8 +104,7 @@ def lib():
             L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
             L.orc_u01.restype = d; L.orc_u01.argtypes = [C.c_uint32]
             L.orc_accept.restype = C.c_int
-            L.orc_accept.argtypes = [C.c_uint32, d, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64,
-                                     C.c_int]
+            L.orc_accept.argtypes = [C.c_uint32, d, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64]
             L.orc_perm_pos.restype = C.c_uint32; L.orc_perm_pos.argtypes = [C.c_uint32, C.c_uint32, u32p]
             L.orc_perm_elem.restype = C.c_uint32; L.orc_perm_elem.argtypes = [C.c_uint32, C.c_uint32, u32p]
             L.orc_sigma_lookup.restype = d
@@ -287,10 +286,13 @@ def u01(r):
     return lib().orc_u01(int(r) & 0xFFFFFFFF)
 
 
-def accept(r, p, c0, cell, step, tag, seed, w):
-    """The accept decision U < p with U = (2^32 r + r' + 1/2) 2^-64, r' word w
-    of the draw (c0, cell, step, tag) under the key seed."""
-    return bool(lib().orc_accept(int(r) & 0xFFFFFFFF, float(p), int(c0), int(cell), int(step), int(tag), int(seed), int(w)))
+def accept(a, p, c0, cell, step, tag, seed):
+    """The accept decision U < p with U = (2^48 a + e + 1/2) 2^-64: a the
+    16-bit first digit, e = 2^16 w0 + (w1 >> 16) from words w0, w1 of the draw
+    (c0, cell, step, tag) under the key seed."""
+    if not 0 <= int(a) < 1 << 16:
+        raise ValueError("the first digit has 16 bits")
+    return bool(lib().orc_accept(int(a), float(p), int(c0), int(cell), int(step), int(tag), int(seed)))
 
 
 def perm_pos(s, n, rk):

@@ -721,32 +721,35 @@ static void philox_at(uint32_t c0, uint32_t cell, uint64_t step, uint32_t tg, ui
     orc_philox4x32_10(ctr, key, out);
 }
 
-/* Where the second word of an accept uniform comes from: word w of the draw
- * (c0, cell, step, tag) with the ACCEPT_EXT purpose. */
-typedef struct { uint32_t c0, cell; uint64_t step; uint32_t tag; uint64_t seed; int w; } accept_src;
+/* Where the rest of an accept uniform comes from: the draw (c0, cell, step,
+ * tag) with the ACCEPT_EXT purpose, its words 0 and 1. */
+typedef struct { uint32_t c0, cell; uint64_t step; uint32_t tag; uint64_t seed; } accept_src;
 
 /* The accept decision U < p (Eq. proba3: the pair collides with probability
- * p = 1 - exp(-x)) for the uniform U = (2^32 r + r' + 1/2) 2^-64, compared
- * digit by digit: the first word r settles it unless r = floor(2^32 p), and
- * only then is the second word r' drawn.  Every p in [0, 1] is honoured
- * down to 2^-64, which per-pair probabilities of rare processes at small
- * time steps need (Trident: ~1e-10 per pair at the paper's 7.4e-3 fs). */
-static int accept_u(uint32_t r, double p, const accept_src *src)
+ * p = 1 - exp(-x)) for the uniform U = (2^48 a + e + 1/2) 2^-64, with a
+ * 16-bit first digit a and a 48-bit rest e = 2^16 w0 + (w1 >> 16) taken from
+ * the extension draw (words w0, w1), compared digit by digit: a settles it
+ * unless a = floor(2^16 p), and only then (probability 2^-16) is e drawn.
+ * Every p in [0, 1] is honoured down to 2^-64, which per-pair probabilities
+ * of rare processes at small time steps need (Trident: ~1e-10 per pair at
+ * the paper's 7.4e-3 fs). */
+static int accept_u(uint32_t a, double p, const accept_src *src)
 {
     if (!(p > 0.0)) return 0;
     if (p >= 1.0) return 1;
-    double X = ldexp(p, 32), fl = floor(X);
-    if ((double)r < fl) return 1;
-    if ((double)r > fl) return 0;
+    double X = ldexp(p, 16), fl = floor(X);
+    if ((double)a < fl) return 1;
+    if ((double)a > fl) return 0;
     uint32_t ext[4];
     philox_at(src->c0, src->cell, src->step, src->tag, src->seed, ext);
-    return (double)ext[src->w] + 0.5 < ldexp(X - fl, 32);
+    uint64_t e = ((uint64_t)ext[0] << 16) | (ext[1] >> 16);
+    return (double)e + 0.5 < ldexp(X - fl, 48);
 }
 
-int orc_accept(uint32_t r, double p, uint32_t c0, uint32_t cell, uint64_t step, uint32_t tg, uint64_t seed, int w)
+int orc_accept(uint32_t a, double p, uint32_t c0, uint32_t cell, uint64_t step, uint32_t tg, uint64_t seed)
 {
-    accept_src src = { c0, cell, step, tg, seed, w };
-    return accept_u(r, p, &src);
+    accept_src src = { c0, cell, step, tg, seed };
+    return accept_u(a, p, &src);
 }
 
 /* Identifier of a secondary: marker bit, step, channel, cell, pair, slot. */
@@ -1012,14 +1015,16 @@ static void pair_of(uint32_t j, uint32_t Np, uint32_t Nt, const uint32_t rk[4], 
  * species but are not projectiles until the next step; ions are never
  * modified.  Random numbers: Philox4x32-10, key = seed, counter
  *   permutation keys:  (0,      cell, step, group | PERM<<4)
- *   accept word r:     e+-: (s>>1, cell, step, group | ACCEPT<<4 | m<<8),
- *                      words 2(s&1) (Brems) and 2(s&1)+1 (Trident);
- *                      photons (one word per pair, BH): (s>>2, ...),
- *                      word s&3; s = projectile slot in id order,
- *                      m = pass index;
- *                      its second word r' (only when r = floor(2^32 p)):
- *                      the same word of the same counter with
- *                      ACCEPT_EXT in place of ACCEPT, see accept_u
+ *   accept digits:     a draw (q, cell, step, group | ACCEPT<<4 | m<<8)
+ *                      holds eight 16-bit digits, digit i being the high
+ *                      (i even) or low (i odd) half of word i>>1;
+ *                      e+-: q = s>>2, digits 2(s&3) (Brems) and
+ *                      2(s&3)+1 (Trident); photons (one digit per pair,
+ *                      BH): q = s>>3, digit s&7; s = projectile slot in
+ *                      id order, m = pass index;
+ *                      the rest of the uniform (only when the digit is
+ *                      floor(2^16 p)): the draw (8q + i, cell, step,
+ *                      group | ACCEPT_EXT<<4 | m<<8), see accept_u
  *   event draws:       (j,      cell, step, group | EVT<<4)
  * with U = ((r >> 9) + 1/2) 2^-23 for the event draws.
  */
@@ -1115,24 +1120,27 @@ int orc_step(const orc_tables *t, int n_cells, const int32_t *material_of_cell,
                 uint32_t s, tau;
                 pair_of(j, Np, Nt, rk, &s, &tau);
                 uint32_t m = Np >= Nt ? 0 : j / Np;
-                /* e+-: two accept words per pair, two pairs per draw;
-                 * photons: one word per pair, four pairs per draw */
-                uint32_t ctr = g < 2 ? s >> 1 : s >> 2;
-                int wd = g < 2 ? (int)(2 * (s & 1)) : (int)(s & 3);
+                /* eight 16-bit digits per draw: e+- pairs take two
+                 * (Brems, Trident), four pairs per draw; photon pairs one
+                 * (BH), eight pairs per draw */
+                uint32_t q = g < 2 ? s >> 2 : s >> 3;
+                uint32_t i = g < 2 ? 2 * (s & 3) : (s & 7);
                 uint32_t acc[4];
-                philox_at(ctr, (uint32_t)cell, step, tag(g, PU_ACCEPT, m), seed, acc);
-                accept_src s1 = { ctr, (uint32_t)cell, step, tag(g, PU_ACCEPT_EXT, m), seed, wd };
+                philox_at(q, (uint32_t)cell, step, tag(g, PU_ACCEPT, m), seed, acc);
+                uint32_t d0 = (i & 1) ? acc[i >> 1] & 0xFFFFu : acc[i >> 1] >> 16;
+                uint32_t d1 = acc[i >> 1] & 0xFFFFu;   /* digit i + 1 (e+-: i is even) */
+                accept_src s1 = { 8 * q + i, (uint32_t)cell, step, tag(g, PU_ACCEPT_EXT, m), seed };
                 accept_src s2 = s1;
-                s2.w += 1;
+                s2.c0 += 1;
                 int ip = pidx[s], it = tidx[tau];
                 if (g < 2) {
                     if (mask & ORC_PROC_BREMS)
-                        cerr |= brems_pair(&c, g, P, ip, ion, it, j, acc[wd], &s1, ph);
+                        cerr |= brems_pair(&c, g, P, ip, ion, it, j, d0, &s1, ph);
                     if (mask & ORC_PROC_TRIDENT)
-                        cerr |= trident_pair(&c, g, P, ip, ion, it, j, acc[wd + 1], &s2, em, ep);
+                        cerr |= trident_pair(&c, g, P, ip, ion, it, j, d1, &s2, em, ep);
                 } else {
                     if (dead[ip]) continue;
-                    if (bh_pair(&c, P, ip, ion, it, j, acc[wd], &s1, em, ep, &cerr)) dead[ip] = 1;
+                    if (bh_pair(&c, P, ip, ion, it, j, d0, &s1, em, ep, &cerr)) dead[ip] = 1;
                 }
             }
             if (cerr) {

@@ -122,8 +122,10 @@ int    orc_tables_build(orc_tables *t);
 /* ---- random numbers and pairing ---- */
 void     orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double   orc_u01(uint32_t r);
-int      orc_accept(uint32_t r, double p, uint32_t c0, uint32_t cell, uint64_t step, uint32_t tag, uint64_t seed,
-                    int w);
+/* U < p for U = (2^48 a + e + 1/2) 2^-64: a the 16-bit first digit, e the
+ * 48-bit rest from words 0, 1 of the draw (c0, cell, step, tag), read only
+ * on a tie a = floor(2^16 p). */
+int      orc_accept(uint32_t a, double p, uint32_t c0, uint32_t cell, uint64_t step, uint32_t tag, uint64_t seed);
 uint32_t orc_perm_pos(uint32_t s, uint32_t n, const uint32_t rk[4]);   /* P^-1(s) */
 uint32_t orc_perm_elem(uint32_t j, uint32_t n, const uint32_t rk[4]);  /* P(j)    */
 

@@ -419,8 +419,8 @@ __device__ __noinline__ EventResult bh_event(const StepArgs* ap, Tab<Real> tb, i
 // ---- one electron/positron - ion pair: Brems then Trident -------------------
 // The weights (projectile *wp, target ion.w) are read only for accepted
 // pairs; no event writes a live particle's weight.  rB, rT: the pair's
-// accept words for Brems and Trident; src names the second word of the
-// Brems uniform (the Trident one is the next word of the same draw).
+// accept digits for Brems and Trident; src names the extension draw of the
+// Brems uniform (the Trident one has the next counter).
 template <typename Real>
 __device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb, int group, int cell, int mat, Real Zf,
                                         Real coef, float u[3], const float* wp, float xpos, int t_slot, uint32_t j,
@@ -465,7 +465,7 @@ __device__ __forceinline__ void ei_pair(const StepArgs* ap, const Tab<Real>& tb,
         const Real x = q_div(coef * sig * f.pp, f.gl * f.gi);
         if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
         AcceptSrc srcT = src;
-        srcT.w += 1;
+        srcT.c0 += 1;   // the Trident digit follows the Brems digit
         if (sig > (Real)0 && accept_u<Real>(rT, -expm1(-x), srcT, a.step, a.seed)) {
             const int ch = group == kGroupEm ? kChTriEm : kChTriEp;
             acc.accepted[ch]++;
@@ -552,7 +552,7 @@ __device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
     if (grp.rank() == 0) acc.pairs[group] += Npair;
     if (Npair > 65536u || (uint32_t)cell > 0xFFFFFFu || a.step > 0x7FFFFull) acc.status |= PCC_ST_ID_RANGE;
     const Real Zf = sizeof(Real) == 8 ? (Real)a.screen[(size_t)mat * kScreenFields + 7] : (Real)a.f_Z[mat];
-    // the FP32 path rejects from the accept word alone above the bounds
+    // the FP32 path rejects from the accept digits alone above the bounds
     const bool quick = sizeof(Real) == 4;
     const uint32_t kB = quick && (a.mask & PCC_BREMS) ? accept_threshold((float)(coef * (Real)a.f_bound[3 * mat])) : 0u;
     const uint32_t kT =
@@ -560,13 +560,15 @@ __device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
     float rad = 0.f, wcre = 0.f;
     bool had = false;
     const bool has_x = P.x != nullptr;
-    for (uint32_t q = grp.rank(); 2 * q < Np; q += grp.size()) {
-        const int nh = (2 * q + 1 < Np) ? 2 : 1;
-        // case A: one pair per projectile, one Philox draw serves both slots
+    // two 16-bit accept digits per pair (Brems, Trident): slots 4q .. 4q + 3
+    // share the draw of counter q, slot 4q + h its digits 2h and 2h + 1
+    for (uint32_t q = grp.rank(); 4 * q < Np; q += grp.size()) {
+        const int nh = Np - 4 * q < 4u ? (int)(Np - 4 * q) : 4;
+        // case A: one pair per projectile, one Philox draw serves four slots
         Philox4 ac{};
         if (pr.caseA) ac = draw(q, cell, a.step, stream_tag(group, kAccept, 0), a.seed);
         for (int h = 0; h < nh; ++h) {
-            const uint32_t s = 2 * q + h;
+            const uint32_t s = 4 * q + h;
             const int sl = p0 + (int)s;
             float u[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
             const float w = P.w[sl];
@@ -574,20 +576,20 @@ __device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
             bool dirty = false;
             if (pr.caseA) {
                 const uint32_t j = pr.pair_of_slot(s);
-                const uint32_t rB = ac.v[2 * h], rT = ac.v[2 * h + 1];
+                const uint32_t rB = accept_digit(ac, 2 * h), rT = accept_digit(ac, 2 * h + 1);
                 if (!quick || rB <= kB || rT <= kT) {
                     if (quick) acc.candidates[group]++;
-                    const AcceptSrc src{q, (uint32_t)cell, stream_tag(group, kAcceptExt, 0), 2 * h};
+                    const AcceptSrc src{8 * q + 2 * h, (uint32_t)cell, stream_tag(group, kAcceptExt, 0)};
                     ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, &w, xp, t0 + (int)(j % Nt), j, rB, rT, src,
                                   acc, rad, wcre, dirty);
                 }
             } else {
                 for (uint32_t m = 0, j = s; j < Nt; ++m, j += Np) {
                     const Philox4 am = draw(q, cell, a.step, stream_tag(group, kAccept, m), a.seed);
-                    const uint32_t rB = am.v[2 * h], rT = am.v[2 * h + 1];
+                    const uint32_t rB = accept_digit(am, 2 * h), rT = accept_digit(am, 2 * h + 1);
                     if (quick && !(rB <= kB || rT <= kT)) continue;
                     acc.candidates[group]++;
-                    const AcceptSrc src{q, (uint32_t)cell, stream_tag(group, kAcceptExt, m), 2 * h};
+                    const AcceptSrc src{8 * q + 2 * h, (uint32_t)cell, stream_tag(group, kAcceptExt, m)};
                     ei_pair<Real>(ap, tb, group, cell, mat, Zf, coef, u, &w, xp, t0 + (int)pr.target_of_pair(j), j,
                                   rB, rT, src, acc, rad, wcre, dirty);
                 }
@@ -638,21 +640,22 @@ __device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
     const bool has_x = P.x != nullptr;
     const bool quick = sizeof(Real) == 4;
     const uint32_t kBH = quick ? accept_threshold((float)(coef * (Real)a.f_bound[3 * mat + 2])) : 0u;
-    // one accept word per pair (BH): slots 4q .. 4q + 3 share the draw of counter q
-    for (uint32_t q = grp.rank(); 4 * q < Np; q += grp.size()) {
-        const int nh = Np - 4 * q < 4u ? (int)(Np - 4 * q) : 4;
+    // one 16-bit accept digit per pair (BH): slots 8q .. 8q + 7 share the
+    // draw of counter q, slot 8q + h its digit h
+    for (uint32_t q = grp.rank(); 8 * q < Np; q += grp.size()) {
+        const int nh = Np - 8 * q < 8u ? (int)(Np - 8 * q) : 8;
         Philox4 ac{};
         if (pr.caseA) ac = draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, 0), a.seed);
         for (int h = 0; h < nh; ++h) {
-            const uint32_t s = 4 * q + h;
+            const uint32_t s = 8 * q + h;
             const int sl = p0 + (int)s;
             const uint32_t npass = pr.caseA ? 1u : (Nt - s + Np - 1) / Np;
             bool loaded = false;
             Real uk[3] = {0, 0, 0}, k = 0;
             for (uint32_t m = 0; m < npass; ++m) {
                 uint32_t j, tau;
-                const uint32_t rw =
-                    pr.caseA ? ac.v[h] : draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed).v[h];
+                const uint32_t rw = accept_digit(
+                    pr.caseA ? ac : draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed), (uint32_t)h);
                 if (quick && !(rw <= kBH)) continue;   // exact quick reject
                 if (pr.caseA) {
                     j = pr.pair_of_slot(s);
@@ -678,7 +681,7 @@ __device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
                 if (!(sig > (Real)0)) continue;
                 const Real x = coef * sig * kp / (k * f.gi);
                 if (x > (Real)1) acc.status |= PCC_ST_PROB_LARGE;
-                const AcceptSrc src{q, (uint32_t)cell, stream_tag(kGroupPh, kAcceptExt, m), h};
+                const AcceptSrc src{8 * q + h, (uint32_t)cell, stream_tag(kGroupPh, kAcceptExt, m)};
                 if (!accept_u<Real>(rw, -expm1(-x), src, a.step, a.seed)) continue;
                 acc.accepted[kChBH]++;
                 const Real fac = d / (f.gi + (Real)1) - k;
@@ -1116,7 +1119,7 @@ __device__ __forceinline__ void flag_cell(const Queue& Q, int cell)
 }
 
 // Acceptance bounds of the group at this coefficient, as thresholds on the
-// accept words: a pair can be accepted only if r <= floor(2^32 b).  The
+// 16-bit accept digits: a pair can be accepted only if a <= floor(2^16 b).  The
 // per-material bounds carry the ion-motion factor 1 + |beta_i| at its
 // largest value 2; for the electrons the scan passes coef times
 // (1 + max |beta_i|)/2 of the cell, which halves their candidates where the
@@ -1176,20 +1179,27 @@ __device__ __forceinline__ bool bh_candidate(const StepArgs& a, const Tab<float>
     return true;
 }
 
-constexpr int kWarpBuf = 256;   // per-warp staging of candidates before the flat queue
+constexpr int kWarpBuf = 512;   // per-warp staging of candidates before the flat queue
 
-// The accept words of projectile slot s (random-stream layout): an e+- pair
-// takes words 2(s&1) (Brems) and 2(s&1)+1 (Trident) of counter s>>1; a photon
-// pair, which has one accept word (BH), word s&3 of counter s>>2.
+// The accept digits of projectile slot s (random-stream layout; a draw holds
+// eight 16-bit digits, see accept_digit): an e+- pair takes digits 2(s&3)
+// (Brems) and 2(s&3)+1 (Trident) of counter s>>2, a photon pair, which has
+// one (BH), digit s&7 of counter s>>3.  The extension draw of digit d of
+// counter q has counter 8q + d: 2s (Brems), 2s + 1 (Trident), s (BH).
 template <int GROUP>
 struct AcceptSlots {
-    static constexpr uint32_t kPerDraw = GROUP == kGroupPh ? 4u : 2u;
-    static __device__ __forceinline__ uint32_t ctr(uint32_t s) { return GROUP == kGroupPh ? s >> 2 : s >> 1; }
-    static __device__ __forceinline__ uint32_t word(uint32_t s) { return GROUP == kGroupPh ? (s & 3u) : 2u * (s & 1u); }
-    // slot kPerDraw q + h of a draw: may the pair be accepted under thresholds k1 (Brems or BH), k2 (Trident)?
+    static constexpr uint32_t kPerDraw = GROUP == kGroupPh ? 8u : 4u;
+    static __device__ __forceinline__ uint32_t ctr(uint32_t s) { return GROUP == kGroupPh ? s >> 3 : s >> 2; }
+    static __device__ __forceinline__ uint32_t digit(uint32_t s) { return GROUP == kGroupPh ? (s & 7u) : 2u * (s & 3u); }
+    static __device__ __forceinline__ uint32_t ext(uint32_t s) { return GROUP == kGroupPh ? s : 2u * s; }
+    // slot kPerDraw q + h of a draw: may the pair be accepted under the digit
+    // thresholds k1 (Brems or BH), k2 (Trident)?  A high half is tested on
+    // the whole word (w >> 16 <= k iff w <= 2^16 k + 0xFFFF).
     static __device__ __forceinline__ bool hit(const Philox4& d, int h, uint32_t k1, uint32_t k2)
     {
-        return GROUP == kGroupPh ? d.v[h] <= k1 : (d.v[2 * h] <= k1 || d.v[2 * h + 1] <= k2);
+        const uint32_t hi1 = (k1 << 16) | 0xFFFFu;
+        if (GROUP == kGroupPh) return (h & 1) ? (d.v[h >> 1] & 0xFFFFu) <= k1 : d.v[h >> 1] <= hi1;
+        return d.v[h] <= hi1 || (d.v[h] & 0xFFFFu) <= k2;
     }
 };
 
@@ -1650,10 +1660,10 @@ __global__ void __launch_bounds__(kBatchedThreads, 4) flat_cand_kernel(const __g
         const uint32_t j = Np <= 32 ? perm_pos_small(s, Np, rk) : perm_pos_large(s, Np, rk);
         const int ts = cm.t0 + (int)fast_mod(j, Nt, 1.0f / (float)Nt);
         using AS = AcceptSlots<GROUP>;
-        const uint32_t wd = AS::word(s);
+        const uint32_t dg = AS::digit(s);
         const Philox4 ph = draw_k(AS::ctr(s), (uint32_t)cell, step32, stream_tag(GROUP, kAccept, 0), a.keys);
-        const uint32_t r1 = ph.v[wd], r2 = GROUP == kGroupPh ? 0u : ph.v[wd + 1];
-        const AcceptSrc src{AS::ctr(s), (uint32_t)cell, stream_tag(GROUP, kAcceptExt, 0), (int)wd};
+        const uint32_t r1 = accept_digit(ph, dg), r2 = GROUP == kGroupPh ? 0u : accept_digit(ph, dg + 1);
+        const AcceptSrc src{AS::ext(s), (uint32_t)cell, stream_tag(GROUP, kAcceptExt, 0)};
         const int sl = cm.p0 + (int)s;
         float rad = 0.f, wcre = 0.f;
         bool event = false;
@@ -1724,10 +1734,10 @@ __global__ void __launch_bounds__(kBatchedThreads, 2) caseb_cand_kernel(const __
                 const uint32_t j = Q.qb[cm.t0 + k];
                 const uint32_t s = j % Np, mp = j / Np;
                 using AS = AcceptSlots<GROUP>;
-                const uint32_t wd = AS::word(s);
+                const uint32_t dg = AS::digit(s);
                 const Philox4 ph = draw_k(AS::ctr(s), (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
-                const uint32_t r1 = ph.v[wd], r2 = GROUP == kGroupPh ? 0u : ph.v[wd + 1];
-                const AcceptSrc src{AS::ctr(s), (uint32_t)cell, stream_tag(GROUP, kAcceptExt, mp), (int)wd};
+                const uint32_t r1 = accept_digit(ph, dg), r2 = GROUP == kGroupPh ? 0u : accept_digit(ph, dg + 1);
+                const AcceptSrc src{AS::ext(s), (uint32_t)cell, stream_tag(GROUP, kAcceptExt, mp)};
                 const uint32_t t = Nt <= 32 ? (uint32_t)tab[j] : perm_elem_large(j, Nt, rk);
                 const int ts = cm.t0 + (int)t, sl = cm.p0 + (int)s;
                 bool event = false;

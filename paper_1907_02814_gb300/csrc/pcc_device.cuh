@@ -64,44 +64,55 @@ __device__ __forceinline__ Philox4 draw(uint32_t c0, uint32_t cell, uint64_t ste
     return philox4x32_10(c0, cell, (uint32_t)step, tag, (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
-// Where the second word of an accept uniform comes from: word w of the draw
+// Where the rest of an accept uniform comes from: words 0 and 1 of the draw
 // (c0, cell, step, group | kAcceptExt << 4 | pass << 8) of the step's seed.
 struct AcceptSrc {
     uint32_t c0, cell, tag;
-    int w;
 };
 
 // The accept decision U < p (Eq. proba3: collision with probability
-// p = 1 - exp(-x)) for the uniform U = (2^32 r + r' + 1/2) 2^-64, read digit
-// by digit: the accept word r settles it unless r = floor(2^32 p), and only
-// then (probability 2^-32) is the second word r' drawn.  Every p is honoured
-// down to 2^-64; a fixed-point uniform would drop probabilities below its
-// resolution.  2^32 p and its fractional part are exact in either precision.
-// The tie (r = floor(2^32 p)): the second word against frac(2^32 p) 2^32.
-static __device__ __noinline__ bool accept_tie(double frac32, uint32_t c0, uint32_t cell, uint32_t tag, int w, uint64_t step,
-                                        uint64_t seed)
+// p = 1 - exp(-x)) for the uniform U = (2^48 a + e + 1/2) 2^-64, read digit
+// by digit: the 16-bit accept digit a settles it unless a = floor(2^16 p),
+// and only then (probability 2^-16) is the 48-bit rest e = 2^16 w0 +
+// (w1 >> 16) drawn.  Every p is honoured down to 2^-64; a fixed-point uniform
+// would drop probabilities below its resolution.  2^16 p and its fractional
+// part are exact in either precision.
+// The tie (a = floor(2^16 p)): the rest against frac(2^16 p) 2^48.
+static __device__ __noinline__ bool accept_tie(double frac48, uint32_t c0, uint32_t cell, uint32_t tag, uint64_t step,
+                                               uint64_t seed)
 {
     const Philox4 e = draw(c0, cell, step, tag, seed);
-    return (double)e.v[w & 3] + 0.5 < frac32;
+    const uint64_t rest = ((uint64_t)e.v[0] << 16) | (e.v[1] >> 16);
+    return (double)rest + 0.5 < frac48;
 }
 
 template <typename Real>
-__device__ __forceinline__ bool accept_u(uint32_t r, Real p, const AcceptSrc& src, uint64_t step, uint64_t seed)
+__device__ __forceinline__ bool accept_u(uint32_t a, Real p, const AcceptSrc& src, uint64_t step, uint64_t seed)
 {
     if (!(p > (Real)0)) return false;
     if (p >= (Real)1) return true;
-    const Real X = p * (Real)4294967296.0, fl = floor(X);
+    const Real X = p * (Real)65536.0, fl = floor(X);
     const uint32_t u = (uint32_t)fl;
-    if (r != u) return r < u;
-    return accept_tie(ldexp((double)(X - fl), 32), src.c0, src.cell, src.tag, src.w, step, seed);
+    if (a != u) return a < u;
+    return accept_tie(ldexp((double)(X - fl), 48), src.c0, src.cell, src.tag, step, seed);
 }
 
-// Quick-reject threshold on the accept word for a bound b >= p: a pair can
-// only be accepted if r <= floor(2^32 b).
+// Digit d (0..7) of an accept draw: the high (d even) or low (d odd) half of
+// word d >> 1.
+__device__ __forceinline__ uint32_t accept_digit(const Philox4& r, uint32_t d)
+{
+    const uint32_t w = r.v[(d >> 1) & 3u];
+    return (d & 1u) ? (w & 0xFFFFu) : (w >> 16);
+}
+
+// Quick-reject threshold on the accept digit for a bound b >= p: a pair can
+// only be accepted if a <= floor(2^16 b).  A non-finite bound lets every pair
+// through to the exact evaluation.
 __device__ __forceinline__ uint32_t accept_threshold(float b)
 {
-    const float X = b * 4294967296.0f;
-    return X >= 4294967040.0f ? 0xFFFFFFFFu : (uint32_t)X;
+    const float X = b * 65536.0f;
+    if (!(X < 65535.0f)) return 0xFFFFu;
+    return X > 0.f ? (uint32_t)X : 0u;
 }
 
 // The same generator with the ten round keys precomputed (key schedule of

@@ -85,7 +85,7 @@ EXPORTS = {
     "pcc_pairing": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.POINTER(Species), C.c_int, C.c_uint64,
                               C.c_uint64, _vp, _vp, _vp]),
     "pcc_totals": (C.c_int, [_vp, C.c_int, C.POINTER(Species), C.c_int, _vp, _vp]),
-    "pcc_accept_check": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.c_uint64, C.c_uint64, _vp, _vp, _vp]),
+    "pcc_accept_check": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_uint64, C.c_uint64, _vp, _vp, _vp]),
     "pcc_totals_noalloc": (C.c_int, [C.c_int, C.POINTER(Species), C.c_int, _vp, _vp]),
     "pcc_read_status": (C.c_int, [_vp, C.POINTER(C.c_uint), C.POINTER(Stats), _vp]),
     "pcc_steps_capture": (C.c_int, [_vp, C.POINTER(StepDesc), C.c_uint64, C.c_int, C.c_int, _vp]),
@@ -341,19 +341,18 @@ def pairing(ctx: Context, n_cells, proj: DeviceSpecies, targ: DeviceSpecies, gro
     return oj, ot
 
 
-def accept_check(r, p, c0, cell, tag, w, step, seed, stream=None):
-    """The kernels' accept decision U < p for device tensors r (int32 view of
-    the uint32 words), p (float64), c0, cell, tag (int32 views), w (int32);
-    returns (out32, out64) int32 tensors of 0/1."""
+def accept_check(r, p, c0, cell, tag, step, seed, stream=None):
+    """The kernels' accept decision U < p for device tensors r (int32, the
+    16-bit accept digits), p (float64), c0, cell, tag (int32 views of the
+    uint32 counter words); returns (out32, out64) int32 tensors of 0/1."""
     import torch
     n = int(r.numel())
     o32 = torch.zeros(n, dtype=torch.int32, device=r.device)
     o64 = torch.zeros(n, dtype=torch.int32, device=r.device)
-    for t, dt in ((r, torch.int32), (p, torch.float64), (c0, torch.int32), (cell, torch.int32), (tag, torch.int32),
-                  (w, torch.int32)):
+    for t, dt in ((r, torch.int32), (p, torch.float64), (c0, torch.int32), (cell, torch.int32), (tag, torch.int32)):
         if t.dtype != dt or not t.is_contiguous() or t.numel() != n:
             raise PccError("accept_check: arrays must be contiguous, of equal length, int32 or float64 (p)")
-    _check(load().pcc_accept_check(n, _ptr(r), _ptr(p), _ptr(c0), _ptr(cell), _ptr(tag), _ptr(w),
+    _check(load().pcc_accept_check(n, _ptr(r), _ptr(p), _ptr(c0), _ptr(cell), _ptr(tag),
                                    C.c_uint64(int(step)), C.c_uint64(int(seed)), _ptr(o32), _ptr(o64),
                                    _stream(stream)), "pcc_accept_check")
     return o32, o64

@@ -104,10 +104,10 @@ int main(void)
            "pcc_expected_emission_bwd");
 
     /* the context-free calls check their arrays and sizes first */
-    expect(pcc_accept_check(-1, u, d, u, u, u, iv, 0, 0, iv, iv, NULL), PCC_E_INVALID, "pcc_accept_check");
-    expect(pcc_accept_check(4, NULL, d, u, u, u, iv, 0, 0, iv, iv, NULL), PCC_E_INVALID, "pcc_accept_check");
-    expect(pcc_accept_check(4, u, d, u, u, u, iv, 0, 0, iv, NULL, NULL), PCC_E_INVALID, "pcc_accept_check");
-    expect(pcc_accept_check(0, NULL, NULL, NULL, NULL, NULL, NULL, 0, 0, NULL, NULL, NULL), PCC_OK,
+    expect(pcc_accept_check(-1, u, d, u, u, u, 0, 0, iv, iv, NULL), PCC_E_INVALID, "pcc_accept_check");
+    expect(pcc_accept_check(4, NULL, d, u, u, u, 0, 0, iv, iv, NULL), PCC_E_INVALID, "pcc_accept_check");
+    expect(pcc_accept_check(4, u, d, u, u, u, 0, 0, iv, NULL, NULL), PCC_E_INVALID, "pcc_accept_check");
+    expect(pcc_accept_check(0, NULL, NULL, NULL, NULL, NULL, 0, 0, NULL, NULL, NULL), PCC_OK,
            "pcc_accept_check");
     expect(pcc_totals_noalloc(1, NULL, 0, d, NULL), PCC_E_INVALID, "pcc_totals_noalloc");
     expect(pcc_totals_noalloc(1, &sp, 0, d, NULL), PCC_E_INVALID, "pcc_totals_noalloc");

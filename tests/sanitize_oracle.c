@@ -245,14 +245,14 @@ int main(void)
     static const double ps[] = {0.0, 1.0, 2.0, 1e-300, 0x1.0p-32, 1.0 - 0x1.0p-40, 0.5};
     for (size_t i = 0; i < sizeof ps / sizeof ps[0]; ++i) {
         double p = ps[i] > 1.0 ? 1.0 : ps[i];
-        uint32_t tie = p >= 1.0 ? 0xFFFFFFFFu : (uint32_t)floor(p * 4294967296.0);
-        for (int w = 0; w < 4; ++w) {
-            orc_accept(tie, ps[i], 7u, 11u, 99u, 6u << 4, 0xABCDEFull, w);
-            orc_accept((uint32_t)sm_next(), ps[i], 7u, 11u, 99u, 6u << 4, 0xABCDEFull, w);
+        uint32_t tie = p >= 1.0 ? 0xFFFFu : (uint32_t)floor(p * 65536.0);
+        for (uint32_t c0 = 0; c0 < 4; ++c0) {
+            orc_accept(tie, ps[i], 7u + c0, 11u, 99u, 6u << 4, 0xABCDEFull);
+            orc_accept((uint32_t)sm_next() & 0xFFFFu, ps[i], 7u + c0, 11u, 99u, 6u << 4, 0xABCDEFull);
         }
     }
-    CHECK(orc_accept(0u, 0.0, 0, 0, 0, 0, 0, 0) == 0, "p = 0 accepts");
-    CHECK(orc_accept(0xFFFFFFFFu, 1.0, 0, 0, 0, 0, 0, 0) == 1, "p = 1 rejects");
+    CHECK(orc_accept(0u, 0.0, 0, 0, 0, 0, 0) == 0, "p = 0 accepts");
+    CHECK(orc_accept(0xFFFFu, 1.0, 0, 0, 0, 0, 0) == 1, "p = 1 rejects");
     for (uint32_t n = 1; n <= 70; n += 23) {
         uint32_t rk[4] = {(uint32_t)sm_next(), (uint32_t)sm_next(), (uint32_t)sm_next(), (uint32_t)sm_next()};
         for (uint32_t j = 0; j < n; ++j)

@@ -116,7 +116,7 @@ def test_batched_flags_only_conditions_met_by_evaluated_pairs(pcc, ctx):
     """The documented difference between the paths: the batched FP32 path
     reads a projectile's momentum only for pairs that pass the quick reject,
     so a NaN momentum and an energy above the table in cells whose pairs are
-    all rejected from their accept words alone raise no status bit there,
+    all rejected from their accept digits alone raise no status bit there,
     while the plain FP64 path, which evaluates every pair, flags both.  With
     dt = 1e-22 s the per-material bound gives an accept threshold of 0, so
     no pair is a candidate; no event happens on either path."""

@@ -529,38 +529,43 @@ def test_case_b_pairs_each_target_once(orc):
 
 # ---------------------------------------------------- accept decision ---
 def test_accept_decision_is_exact(orc):
-    """The accept decision compares U = (2^32 r + r' + 1/2) 2^-64 with the
-    collision probability p exactly: checked in rational arithmetic for
-    probabilities from 1e-15 to 1 - 1e-9, with r on, just below and just
-    above floor(2^32 p) (the tie draws the second word r')."""
+    """The accept decision compares U = (2^48 a + e + 1/2) 2^-64 with the
+    collision probability p exactly, e = 2^16 w0 + (w1 >> 16) from the
+    extension draw: checked in rational arithmetic for probabilities from
+    1e-15 to 1 - 1e-9, with the 16-bit digit a on, just below and just above
+    floor(2^16 p) (the tie reads e)."""
     from fractions import Fraction
     rng = np.random.default_rng(5)
     seed, cell, step = 0x1234ABCD5678, 77, 9
-    ps = [1e-15, 3.3e-11, 2.0 ** -32, 7.7e-10, 1.234e-7, 5.9e-8, 0.01, 0.5, 1.0 - 1e-9] + list(rng.uniform(0, 1e-6, 20))
+    ps = [1e-15, 3.3e-11, 2.0 ** -32, 2.0 ** -16, 7.7e-10, 1.234e-7, 5.9e-8, 1.5e-5, 0.01, 0.5, 1.0 - 1e-9] \
+        + list(rng.uniform(0, 1e-3, 20))
     n = 0
     for p in ps:
-        fl = int(Fraction(p) * 2 ** 32)
-        for r in {max(fl - 1, 0), fl, min(fl + 1, 2 ** 32 - 1), int(rng.integers(0, 2 ** 32))}:
-            for w in (0, 3):
-                c0, tg = int(rng.integers(0, 1000)), 1 | (6 << 4) | (2 << 8)
-                r2 = orc.philox([c0, cell, step, tg], [seed & 0xFFFFFFFF, seed >> 32])[w]
-                exact = Fraction(2 ** 32 * r + r2) + Fraction(1, 2) < Fraction(p) * 2 ** 64
-                assert orc.accept(r, p, c0, cell, step, tg, seed, w) == exact, (p, r, w)
+        fl = int(Fraction(p) * 2 ** 16)
+        for a in {max(fl - 1, 0), fl, min(fl + 1, 2 ** 16 - 1), int(rng.integers(0, 2 ** 16))}:
+            for _ in range(2):
+                c0, tg = int(rng.integers(0, 1 << 17)), 1 | (6 << 4) | (2 << 8)
+                w = orc.philox([c0, cell, step, tg], [seed & 0xFFFFFFFF, seed >> 32])
+                e = (w[0] << 16) | (w[1] >> 16)
+                exact = Fraction(2 ** 48 * a + e) + Fraction(1, 2) < Fraction(p) * 2 ** 64
+                assert orc.accept(a, p, c0, cell, step, tg, seed) == exact, (p, a)
                 n += 1
     assert n > 150
-    assert not orc.accept(0, 0.0, 0, 0, 0, 0, 0, 0) and orc.accept(2 ** 32 - 1, 1.0, 0, 0, 0, 0, 0, 0)
+    assert not orc.accept(0, 0.0, 0, 0, 0, 0, 0) and orc.accept(2 ** 16 - 1, 1.0, 0, 0, 0, 0, 0)
+    with pytest.raises(ValueError):
+        orc.accept(1 << 16, 0.5, 0, 0, 0, 0, 0)
 
 
 def test_tiny_probabilities_are_honoured(orc):
     """A per-pair probability far below the 23-bit resolution of the event
-    uniforms is still taken at its value: over all 2^32 first words the
-    decision accepts floor(2^32 p) of them outright and leaves exactly one to
-    the second word, so P(accept) = p to 2^-64."""
-    for p in (3e-11, 2.5e-9, 4e-8):
-        fl = math.floor(p * 2 ** 32)
-        assert orc.accept(fl - 1, p, 0, 0, 0, 0, 0, 0) if fl > 0 else True
-        assert not orc.accept(fl + 1, p, 0, 0, 0, 0, 0, 0)
-        # the tie: over many second words the fraction accepted is frac(2^32 p)
-        acc = sum(orc.accept(fl, p, c0, 1, 2, 3, 99, 0) for c0 in range(4000))
-        frac = p * 2 ** 32 - fl
+    uniforms is still taken at its value: over all 2^16 first digits the
+    decision accepts floor(2^16 p) of them outright and leaves exactly one to
+    the rest e, so P(accept) = p to 2^-64."""
+    for p in (3e-11, 2.5e-9, 4e-8, 1e-3):
+        fl = math.floor(p * 2 ** 16)
+        assert orc.accept(fl - 1, p, 0, 0, 0, 0, 0) if fl > 0 else True
+        assert not orc.accept(fl + 1, p, 0, 0, 0, 0, 0)
+        # the tie: over many extension draws the fraction accepted is frac(2^16 p)
+        acc = sum(orc.accept(fl, p, c0, 1, 2, 3, 99) for c0 in range(4000))
+        frac = p * 2 ** 16 - fl
         assert abs(acc / 4000 - frac) < 4 * math.sqrt(frac * (1 - frac) / 4000) + 1e-3
