@@ -1514,12 +1514,18 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
             const bool valid = (G == 32 || it < itB) && i < units;
             const uint32_t mp = valid ? i / Qn : 0u, q = valid ? i - mp * Qn : 0u;
             const Philox4 ph = draw_k(q, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
+            bool c[S], anyc = false;
 #pragma unroll
             for (int h = 0; h < (int)S; ++h) {
-                const uint32_t s = S * q + h, j = s + mp * Np;
-                const bool cand = valid && s < Np && j < Nt && AS::hit(ph, h, k1, k2);
-                const unsigned m = __ballot_sync(kFull, cand);
-                if (cand) Q.qb[t0 + cnt + __popc(m & gmask & below)] = j;
+                const uint32_t s = S * q + h;
+                c[h] = valid && s < Np && s + mp * Np < Nt && AS::hit(ph, h, k1, k2);
+                anyc |= c[h];
+            }
+            if (!__any_sync(kFull, anyc)) continue;   // the common case: no candidate in the warp
+#pragma unroll
+            for (int h = 0; h < (int)S; ++h) {
+                const unsigned m = __ballot_sync(kFull, c[h]);
+                if (c[h]) Q.qb[t0 + cnt + __popc(m & gmask & below)] = S * q + h + mp * Np;
                 cnt += __popc(m & gmask);
             }
         }

@@ -48,7 +48,7 @@ struct pcc_ctx {
     // classes (two per octave of N_pair) from which a cell takes a whole
     // warp, 16, 8 or 4 lanes (below: 2).  Chosen by timing on the 2^20-cell
     // batched Cu workload; the autotuner may replace them.
-    int scan_thr[3][4] = {{20, 18, 15, 2}, {12, 12, 6, 0}, {19, 16, 15, 13}};
+    int scan_thr[3][4] = {{20, 20, 15, 2}, {12, 12, 6, 0}, {17, 17, 15, 13}};
     int blocks_per_sm = 0;         // persistent grid cap (0: as many as fit)
     bool class_smem_ready = false; // large shared memory enabled for the class-sort offsets
     int wait_polls = 1 << 22;      // bounded waits give up after this many polls (fault injection: 0)
