@@ -561,14 +561,12 @@ __device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
     bool had = false;
     const bool has_x = P.x != nullptr;
     // two 16-bit accept digits per pair (Brems, Trident): slots 4q .. 4q + 3
-    // share the draw of counter q, slot 4q + h its digits 2h and 2h + 1
-    for (uint32_t q = grp.rank(); 4 * q < Np; q += grp.size()) {
-        const int nh = Np - 4 * q < 4u ? (int)(Np - 4 * q) : 4;
-        // case A: one pair per projectile, one Philox draw serves four slots
-        Philox4 ac{};
-        if (pr.caseA) ac = draw(q, cell, a.step, stream_tag(group, kAccept, 0), a.seed);
-        for (int h = 0; h < nh; ++h) {
-            const uint32_t s = 4 * q + h;
+    // share the draw of counter q, slot 4q + h its digits 2h and 2h + 1.  A
+    // thread per slot (each takes its own copy of the draw), so that small
+    // cells keep their threads busy.
+    for (uint32_t s = grp.rank(); s < Np; s += grp.size()) {
+        const uint32_t q = s >> 2, h = s & 3u;
+        {
             const int sl = p0 + (int)s;
             float u[3] = {P.ux[sl], P.uy[sl], P.uz[sl]};
             const float w = P.w[sl];
@@ -576,6 +574,7 @@ __device__ void ei_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
             bool dirty = false;
             if (pr.caseA) {
                 const uint32_t j = pr.pair_of_slot(s);
+                const Philox4 ac = draw(q, cell, a.step, stream_tag(group, kAccept, 0), a.seed);
                 const uint32_t rB = accept_digit(ac, 2 * h), rT = accept_digit(ac, 2 * h + 1);
                 if (!quick || rB <= kB || rT <= kT) {
                     if (quick) acc.candidates[group]++;
@@ -641,21 +640,18 @@ __device__ void bh_cell(const G& grp, const StepArgs* ap, const Tab<Real>& tb, i
     const bool quick = sizeof(Real) == 4;
     const uint32_t kBH = quick ? accept_threshold((float)(coef * (Real)a.f_bound[3 * mat + 2])) : 0u;
     // one 16-bit accept digit per pair (BH): slots 8q .. 8q + 7 share the
-    // draw of counter q, slot 8q + h its digit h
-    for (uint32_t q = grp.rank(); 8 * q < Np; q += grp.size()) {
-        const int nh = Np - 8 * q < 8u ? (int)(Np - 8 * q) : 8;
-        Philox4 ac{};
-        if (pr.caseA) ac = draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, 0), a.seed);
-        for (int h = 0; h < nh; ++h) {
-            const uint32_t s = 8 * q + h;
+    // draw of counter q, slot 8q + h its digit h; a thread per slot
+    for (uint32_t s = grp.rank(); s < Np; s += grp.size()) {
+        const uint32_t q = s >> 3, h = s & 7u;
+        {
             const int sl = p0 + (int)s;
             const uint32_t npass = pr.caseA ? 1u : (Nt - s + Np - 1) / Np;
             bool loaded = false;
             Real uk[3] = {0, 0, 0}, k = 0;
             for (uint32_t m = 0; m < npass; ++m) {
                 uint32_t j, tau;
-                const uint32_t rw = accept_digit(
-                    pr.caseA ? ac : draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed), (uint32_t)h);
+                const uint32_t rw =
+                    accept_digit(draw(q, cell, a.step, stream_tag(kGroupPh, kAccept, m), a.seed), h);
                 if (quick && !(rw <= kBH)) continue;   // exact quick reject
                 if (pr.caseA) {
                     j = pr.pair_of_slot(s);
