@@ -1008,6 +1008,23 @@ __device__ __forceinline__ uint32_t fast_mod(uint32_t j, uint32_t n, float inv_n
     return (uint32_t)r;
 }
 
+// i = quot n + rem for n >= 1 by a float reciprocal (inv_n = 1/n), exact: the
+// estimate is off by at most one below 2^24, and larger i divide exactly.
+__device__ __forceinline__ void div_small(uint32_t i, uint32_t n, float inv_n, uint32_t& quot, uint32_t& rem)
+{
+    if (i >= (1u << 24)) {
+        quot = i / n;
+        rem = i - quot * n;
+        return;
+    }
+    uint32_t qq = __float2uint_rz((float)i * inv_n);
+    int r = (int)i - (int)(qq * n);
+    if (r < 0) { r += (int)n; --qq; }
+    if (r >= (int)n) { r -= (int)n; ++qq; }
+    quot = qq;
+    rem = (uint32_t)r;
+}
+
 // Per-cell summary of the ions written by the electron scan, which reads
 // every ion of its cells anyway, for the positron and photon scans of the
 // same call: x = n_t (the electron scan's FP32 sum), y = w0 (first ion
@@ -1400,7 +1417,8 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
                     u2s += u2;
                 }
             }
-            if constexpr (kWriter) b2 = isfinite(u2s) ? u2m / (1.f + u2m) : 1.f;
+            // (u^2 >= 1e30 gives beta^2 = 1 to float precision)
+            if constexpr (kWriter) b2 = isfinite(u2s) && u2m < 1e30f ? __fdividef(u2m, 1.f + u2m) : 1.f;
             else b2 = (uint32_t)gl < Nt ? 1.f : 0.f;
         }
         const float st_sum = group_sum<G>(st);
@@ -1408,7 +1426,13 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
         // 1 + max |beta_i| of the cell, rounded up past the few ulps of its
         // float evaluation (2 without the summary in the other scans)
         const float bmax = group_max<G>(b2);
-        const float bfac = have ? fabsf(is.z) : fminf((1.f + sqrtf(fminf(bmax, 1.f))) * (1.f + 0x1p-20f), 2.f);
+        float bfac;
+        if (have) {
+            bfac = fabsf(is.z);
+        } else {   // sqrt as b rsqrt(b): its few-ulp error is far inside the 2^-20 margin
+            const float bm = fminf(bmax, 1.f);
+            bfac = fminf((1.f + (bm > 0.f ? bm * rsqrtf(bm) : 0.f)) * (1.f + 0x1p-20f), 2.f);
+        }
         if constexpr (kWriter) {
             if (active && gl == 0)
                 IC.sum[cell] = make_float4(n_t, w0, uni ? bfac : -bfac, __uint_as_float(*IC.serial));
@@ -1431,11 +1455,12 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
                 sp += wp;
                 sf += fminf(wp, w0);
             }
-        } else {   // projectile s takes part in ceil((N_t - s) / N_p) pairs
+        } else {   // projectile s takes part in ceil((N_t - s) / N_p) = q0 + [s < r0] pairs, N_t = q0 N_p + r0
+            const uint32_t q0 = Nt / Np, r0 = Nt - q0 * Np;
             for (uint32_t s = gl; s < Np; s += G) {
                 const float wp = P.w[p0 + s];
                 sp += wp;
-                sf += fminf(wp, w0) * (float)((Nt - s + Np - 1) / Np);
+                sf += fminf(wp, w0) * (float)(q0 + (s < r0 ? 1u : 0u));
             }
         }
         const float n_p = group_sum<G>(sp);
@@ -1501,28 +1526,32 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
         // i = m Qn + q covers slots S q .. S q + S - 1 of pass m, i.e. pairs
         // j = s + m N_p.  A group's lanes take consecutive units, so each
         // projectile's pairs are queued in increasing j.
-        const uint32_t Qn = (Np + S - 1) / S, passes = Np ? (Nt + Np - 1) / Np : 0u, units = Qn * passes;
-        const uint32_t itB = active && !caseA ? (units + G - 1) / G : 0u;
-        const uint32_t nitB = G == 32 ? itB : __reduce_max_sync(kFull, itB);
         uint32_t cnt = 0;
-        for (uint32_t it = 0; it < nitB; ++it) {
-            const uint32_t i = it * G + gl;
-            const bool valid = (G == 32 || it < itB) && i < units;
-            const uint32_t mp = valid ? i / Qn : 0u, q = valid ? i - mp * Qn : 0u;
-            const Philox4 ph = draw_k(q, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
-            bool c[S], anyc = false;
+        if (__any_sync(kFull, active && !caseA)) {   // most warps hold no such cell
+            const uint32_t Qn = (Np + S - 1) / S, passes = Np ? (Nt + Np - 1) / Np : 0u, units = Qn * passes;
+            const uint32_t itB = active && !caseA ? (units + G - 1) / G : 0u;
+            const uint32_t nitB = G == 32 ? itB : __reduce_max_sync(kFull, itB);
+            const float inv_qn = Qn ? 1.0f / (float)Qn : 0.f;
+            for (uint32_t it = 0; it < nitB; ++it) {
+                const uint32_t i = it * G + gl;
+                const bool valid = (G == 32 || it < itB) && i < units;
+                uint32_t mp = 0u, q = 0u;
+                if (valid) div_small(i, Qn, inv_qn, mp, q);
+                const Philox4 ph = draw_k(q, (uint32_t)cell, step32, stream_tag(GROUP, kAccept, mp), a.keys);
+                bool c[S], anyc = false;
 #pragma unroll
-            for (int h = 0; h < (int)S; ++h) {
-                const uint32_t s = S * q + h;
-                c[h] = valid && s < Np && s + mp * Np < Nt && AS::hit(ph, h, k1, k2);
-                anyc |= c[h];
-            }
-            if (!__any_sync(kFull, anyc)) continue;   // the common case: no candidate in the warp
+                for (int h = 0; h < (int)S; ++h) {
+                    const uint32_t s = S * q + h;
+                    c[h] = valid && s < Np && s + mp * Np < Nt && AS::hit(ph, h, k1, k2);
+                    anyc |= c[h];
+                }
+                if (!__any_sync(kFull, anyc)) continue;   // the common case: no candidate in the warp
 #pragma unroll
-            for (int h = 0; h < (int)S; ++h) {
-                const unsigned m = __ballot_sync(kFull, c[h]);
-                if (c[h]) Q.qb[t0 + cnt + __popc(m & gmask & below)] = S * q + h + mp * Np;
-                cnt += __popc(m & gmask);
+                for (int h = 0; h < (int)S; ++h) {
+                    const unsigned m = __ballot_sync(kFull, c[h]);
+                    if (c[h]) Q.qb[t0 + cnt + __popc(m & gmask & below)] = S * q + h + mp * Np;
+                    cnt += __popc(m & gmask);
+                }
             }
         }
         if (!caseA) ncand = cnt;
