@@ -1192,8 +1192,6 @@ __device__ __forceinline__ bool bh_candidate(const StepArgs& a, const Tab<float>
     return true;
 }
 
-constexpr int kWarpBuf = 512;   // per-warp staging of candidates before the flat queue
-
 // The accept digits of projectile slot s (random-stream layout; a draw holds
 // eight 16-bit digits, see accept_digit): an e+- pair takes digits 2(s&3)
 // (Brems) and 2(s&3)+1 (Trident) of counter s>>2, a photon pair, which has
@@ -1306,6 +1304,8 @@ __device__ __forceinline__ float npt_over_pairs(const StepArgs& a, const Species
     return warp_sum(spt);
 }
 
+constexpr int kWarpBuf = 256;   // per-warp staging of candidates before the flat queue
+
 // Scan state of one warp, carried from one size-class segment to the next.
 struct ScanWarp {
     int nb;                              // candidates staged in the warp buffer (warp-uniform)
@@ -1324,11 +1324,53 @@ __device__ __forceinline__ void flush_staged(const Queue& Q, const uint2* wb, in
     __syncwarp();
 }
 
+// Stage the candidates a lane marked in cmask (bit (it - it0) S + h: slot
+// S (it G + gl) + h of its cell, iteration it of the accept loop) in the
+// warp's buffer, after a warp-wide prefix of the counts; a buffer that would
+// overflow goes to the flat queue first, and a batch larger than the buffer
+// (every pair a candidate) straight to it.  All 32 lanes call it.
+template <int G, uint32_t S>
+__device__ __forceinline__ void emit_candidates(const Queue& Q, uint2* wb, ScanWarp& sw, int cell, uint32_t cmask,
+                                                uint32_t it0, int gl, int lane, BlockAcc& bacc)
+{
+    const uint32_t n = __popc(cmask);
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = (int)__shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    if (sw.nb + total > kWarpBuf) {
+        flush_staged(Q, wb, sw.nb, bacc, lane);
+        sw.nb = 0;
+    }
+    const bool direct = total > kWarpBuf;
+    uint32_t base = (uint32_t)sw.nb;
+    if (direct) {
+        if (lane == 0) base = (uint32_t)atomicAdd(Q.flat_count, total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane == 0 && base + (uint32_t)total > Q.cap_flat) atomicOr(&bacc.status, PCC_ST_CAPACITY);
+    }
+    uint32_t k = base + incl - n;
+    while (cmask) {
+        const uint32_t b = (uint32_t)(__ffs(cmask) - 1);
+        cmask &= cmask - 1u;
+        const uint2 e = make_uint2((uint32_t)cell, ((it0 + b / S) * G + (uint32_t)gl) * S + b % S);
+        if (!direct) wb[k] = e;
+        else if (k < Q.cap_flat) Q.flat[k] = e;
+        ++k;
+    }
+    if (!direct) sw.nb += total;
+}
+
 // The cells of list entries [e0, e1), taken C = 32 / G at a time by a warp:
-// lane group g (lanes gG .. gG + G - 1) owns one cell, its lane l owns slots
-// base + 2l and base + 2l + 1 per pass, whose accept uniforms are the four
-// words of the lane's Philox draw (the counter depends on the slot, not on
-// the lane, so the random stream does not depend on G).  Tuples of C
+// lane group g (lanes gG .. gG + G - 1) owns one cell, its lane l owns the
+// S slots base + S l .. base + S l + S - 1 per pass, whose accept digits are
+// those of the lane's Philox draw (S = 4 for e+-, 8 for photons; the counter
+// depends on the slot, not on the lane, so the random stream does not depend
+// on G).  Tuples of C
 // entries are dealt to the warps round-robin starting at tuple t_first.
 // Loops that hold ballots run to the largest trip count of the warp's
 // groups, so every collective is reached by all 32 lanes.
@@ -1496,28 +1538,51 @@ __device__ __forceinline__ void scan_segment(const StepArgs& a, const CellList& 
         const uint32_t nitA = G == 32 ? itA : __reduce_max_sync(kFull, itA);
         const PhiloxFixed pf = philox_fixed((uint32_t)cell, step32, stream_tag(GROUP, kAccept, 0), a.keys);
         uint32_t mine = 0;   // candidates of this lane
-        for (uint32_t it = 0; it < nitA; ++it) {
-            const Philox4 ph = draw_fixed(it * G + gl, pf, a.keys);
-            const bool live = G == 32 || it < itA;
-            const uint32_t s0 = (it * G + gl) * S;
-            bool c[S], anyc = false;
+        if constexpr (GROUP != kGroupPh) {
+            // e+-: candidates are marked in a per-lane mask, 32 / S
+            // iterations per mask, and staged when it is full or the loop ends
+            constexpr uint32_t kIt = 32 / S;
+            uint32_t cmask = 0, it0 = 0;
+            for (uint32_t it = 0; it < nitA; ++it) {
+                const Philox4 ph = draw_fixed(it * G + gl, pf, a.keys);
+                const uint32_t s0 = (it * G + gl) * S;
+                const uint32_t lim = (G == 32 || it < itA) && s0 < Np ? Np - s0 : 0u;   // live slots of the draw
 #pragma unroll
-            for (int h = 0; h < (int)S; ++h) {
-                c[h] = live && s0 + h < Np && AS::hit(ph, h, k1, k2);
-                anyc |= c[h];
+                for (int h = 0; h < (int)S; ++h)
+                    if ((uint32_t)h < lim && AS::hit(ph, h, k1, k2)) cmask |= 1u << ((it - it0) * S + h);
+                if (it - it0 == kIt - 1 || it + 1 == nitA) {   // warp-uniform
+                    mine += __popc(cmask);
+                    emit_candidates<G, S>(Q, wb, sw, cell, cmask, it0, gl, lane, bacc);
+                    cmask = 0;
+                    it0 = it + 1;
+                }
             }
-            // most iterations of small cells have no candidate in the warp
-            if (__any_sync(kFull, anyc)) {
+        } else {
+            // photons (rarer candidates, eight slots a draw): a vote per
+            // iteration, ballots only when some lane has a candidate
+            for (uint32_t it = 0; it < nitA; ++it) {
+                const Philox4 ph = draw_fixed(it * G + gl, pf, a.keys);
+                const bool live = G == 32 || it < itA;
+                const uint32_t s0 = (it * G + gl) * S;
+                bool c[S];
+                uint32_t nc = 0;
 #pragma unroll
                 for (int h = 0; h < (int)S; ++h) {
-                    const unsigned m = __ballot_sync(kFull, c[h]);
-                    if (c[h]) wb[sw.nb + __popc(m & below)] = make_uint2((uint32_t)cell, s0 + h);
-                    sw.nb += __popc(m);
-                    mine += (uint32_t)c[h];
+                    c[h] = live && s0 + h < Np && AS::hit(ph, h, k1, k2);
+                    nc += (uint32_t)c[h];
                 }
-                if (sw.nb > kWarpBuf - 32 * (int)S) {   // flush before the next iteration could overfill it
-                    flush_staged(Q, wb, sw.nb, bacc, lane);
-                    sw.nb = 0;
+                if (__any_sync(kFull, nc != 0)) {
+                    if (sw.nb + (int)__reduce_add_sync(kFull, nc) > kWarpBuf) {   // room for this iteration's candidates
+                        flush_staged(Q, wb, sw.nb, bacc, lane);
+                        sw.nb = 0;
+                    }
+#pragma unroll
+                    for (int h = 0; h < (int)S; ++h) {
+                        const unsigned m = __ballot_sync(kFull, c[h]);
+                        if (c[h]) wb[sw.nb + __popc(m & below)] = make_uint2((uint32_t)cell, s0 + h);
+                        sw.nb += __popc(m);
+                        mine += (uint32_t)c[h];
+                    }
                 }
             }
         }
