@@ -96,6 +96,22 @@ def test_long_time_step_is_flagged(pcc, ctx, orc, precision):
     assert stats[0]["accepted"][0] == 8 * 32
 
 
+def test_every_pair_a_candidate_in_large_cells(pcc, ctx, orc):
+    """Large cells (2048 electrons, scanned by whole warps) in a step so long
+    that every pair collides: every pair is then a candidate, more than the
+    scan's per-warp staging holds at once, and all of them reach the queue
+    (the accepted pairs equal the oracle's: all but those whose electron lies
+    below the Brems threshold)."""
+    wl = W.solid_cu(n_cells=2, e_per_cell=2048, i_per_cell=16, seed=44, dt=1e-7, T_mev=5.0)
+    _, status, stats = run(pcc, ctx, wl, "fp32", mask=1)
+    assert status & pcc.ST_PROB_LARGE     # (the photon store overflows too: 2048 new photons per cell)
+    assert stats[0]["pairs"][0] == 2 * 2048
+    assert stats[0]["candidates"][0] == 2 * 2048
+    ost = oracle_status(orc, wl, mask=1)
+    assert int(ost["status"]) & 2
+    assert stats[0]["accepted"][0] == int(ost["accepted"][0]) > 2 * 2048 - 16
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_nonfinite_momentum_is_flagged(pcc, ctx, precision):
     """A NaN momentum: PCC_ST_NONFINITE; the step finishes and every pair is
