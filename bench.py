@@ -611,10 +611,19 @@ def e2e_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, 
     live_bytes = 24 * sum(int(state[k].cell_count.sum()) for k in names)
     n = max(1, min(args.steps, 5))
 
-    def one_step(s):
+    cur = torch.cuda.current_stream()
+    copy_ms = []
+
+    def one_step(s, timed=False):
+        if timed:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
         for k in names:
             for f in fields:
                 getattr(state[k], f).copy_(host[k][f], non_blocking=True)
+        if timed:
+            e1.record(cur)
+            copy_ms.append((e0, e1))
         pcc.collide(ctx, n_cells, mat_of_cell, ion_mass, state["em"], state["ep"], state["ph"], dev["ion"], dt, seed,
                     10_000 + s, precision=prec, ledger=ledger)
         for k in names:
@@ -626,14 +635,15 @@ def e2e_measure(args, ctx, pcc, torch, dev, n_cells, mat_of_cell, ion_mass, dt, 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in range(n):
-        status, st = one_step(s)
+        status, st = one_step(s, timed=True)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
+    h2d_ms = float(np.mean([a.elapsed_time(b) for a, b in copy_ms]))
     pairs = sum(st["pairs"])
     del state, host
     return {"value": pairs / (el / n), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "live_record_bytes_per_step": int(live_bytes), "steps": n, "status": status,
-            "ms_per_step": 1e3 * el / n, "h2d_gbs_measured": h2d_rate(torch)}
+            "ms_per_step": 1e3 * el / n, "h2d_ms_per_step": h2d_ms, "h2d_gbs_measured": h2d_rate(torch)}
 
 
 # ---------------------------------------------------------- CPU oracle leg --
